@@ -1,0 +1,303 @@
+"""Pins for the oracle (CPU only).
+
+The oracle is checked against things other than itself: the hand cases under
+tests/golden (labels derived by hand from the paper's definitions), an
+independent O(n^2) brute force from the definitions (tests/brute.py), the
+friends-of-friends = connected-components identity, exact-arithmetic checks of
+the FP32 predicate, invariants, and planted mistakes that the pins must catch.
+"""
+import os
+import shutil
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import brute
+import oracle
+from conftest import golden_cases
+from workloads import CONFIGS, clumps, uniform
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# ---- hand cases -------------------------------------------------------------
+
+@pytest.mark.parametrize("case", golden_cases(), ids=lambda c: c[0])
+def test_golden_oracle(case):
+    name, p, eps, minpts, want = case
+    got = oracle.dbscan(p, eps, minpts)
+    assert np.array_equal(got, want), f"{name}: {got} != {want}"
+
+
+@pytest.mark.parametrize("case", golden_cases(), ids=lambda c: c[0])
+def test_golden_brute(case):
+    """The brute force agrees with the hand-derived labels too."""
+    name, p, eps, minpts, want = case
+    assert np.array_equal(brute.dbscan(p, eps, minpts), want), name
+
+
+# ---- the predicate, by exact arithmetic ----------------------------------------
+
+def _rn32(x: Fraction) -> Fraction:
+    """Round an exact rational to the nearest FP32 (ties to even); values here
+    are far from the subnormal range and fit a float64 exactly before rounding."""
+    d = float(x)
+    assert Fraction(d) == x, "intermediate not exact in float64"
+    return Fraction(float(np.float32(d)))
+
+
+def _pred_exact(p, q, eps) -> bool:
+    P = [Fraction(float(v)) for v in np.asarray(p, np.float32)]
+    Q = [Fraction(float(v)) for v in np.asarray(q, np.float32)]
+    e = Fraction(float(np.float32(eps)))
+    d = [_rn32(a - b) for a, b in zip(P, Q)]
+    sq = [_rn32(v * v) for v in d]
+    d2 = _rn32(_rn32(sq[0] + sq[1]) + sq[2])
+    return d2 <= _rn32(e * e)
+
+
+def test_fma_case_by_exact_arithmetic():
+    case = [c for c in golden_cases() if c[0] == "fma_contraction.txt"][0]
+    _, p, eps, _, _ = case
+    assert _pred_exact(p[0], p[1], eps) is True
+    assert _pred_exact(p[0], p[2], eps) is False
+    assert oracle.pred(p[0], p[1], eps) is True
+    assert oracle.pred(p[0], p[2], eps) is False
+
+
+def test_pred_random_exact():
+    rng = np.random.default_rng(11)
+    for _ in range(3000):
+        p = rng.random(3).astype(np.float32)
+        q = (p + rng.normal(0, 0.3, 3)).astype(np.float32)
+        eps = np.float32(rng.uniform(0.2, 0.6))
+        assert oracle.pred(p, q, eps) == _pred_exact(p, q, eps)
+
+
+# ---- brute force on small random inputs ---------------------------------------
+
+def _clumpy(rng, n, k, spread, noise_frac=0.3):
+    c = rng.random((k, 3))
+    own = rng.integers(0, k, n)
+    p = c[own] + rng.normal(0, spread, (n, 3))
+    m = int(noise_frac * n)
+    p[:m] = rng.random((m, 3))
+    return p.astype(np.float32)
+
+
+def _cases():
+    rng = np.random.default_rng(123)
+    out = []
+    for n, eps, minpts in [(500, 0.08, 2), (800, 0.06, 3), (1000, 0.05, 5), (700, 0.1, 10),
+                           (300, 0.2, 1), (1500, 0.04, 4)]:
+        out.append((f"uniform-{n}-{minpts}", rng.random((n, 3)).astype(np.float32), eps, minpts))
+    for n, eps, minpts in [(1200, 0.02, 2), (1500, 0.03, 5), (2000, 0.025, 10), (900, 0.05, 3)]:
+        out.append((f"clumpy-{n}-{minpts}", _clumpy(rng, n, 8, 0.02), eps, minpts))
+    # duplicates and exact lattice spacings (distances exactly eps)
+    lat = np.stack(np.meshgrid(*[np.arange(6)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    lat = (lat * 0.125).astype(np.float32)
+    keep = rng.random(len(lat)) < 0.7
+    out.append(("lattice-fof", lat[keep], 0.125, 2))
+    out.append(("lattice-dbscan", lat[keep], 0.125, 5))
+    out.append(("lattice-diag", lat[keep], float(np.float32(0.125 * np.sqrt(2))), 7))
+    dup = rng.random((200, 3)).astype(np.float32)
+    dup = np.concatenate([dup, dup[rng.integers(0, 200, 300)]])
+    out.append(("duplicates-eps0", dup, 0.0, 2))
+    out.append(("duplicates-eps0-m3", dup, 0.0, 3))
+    out.append(("duplicates-small", dup, 0.03, 4))
+    planar = rng.random((1000, 3)).astype(np.float32)
+    planar[:, 2] = 0.5
+    out.append(("planar", planar, 0.04, 3))
+    line = np.zeros((400, 3), np.float32)
+    line[:, 0] = np.sort(rng.random(400)).astype(np.float32)
+    out.append(("line", line, 0.003, 2))
+    one = np.array([[0.3, 0.2, 0.1]], np.float32)
+    out.append(("single", one, 0.1, 1))
+    out.append(("single-noise", one, 0.1, 2))
+    # negative and large coordinates, off-centre box
+    off = (rng.random((800, 3)) * 40 - 20).astype(np.float32)
+    out.append(("offset", off, 1.6, 3))
+    # the C-config mixtures at small sizes
+    out.append(("clumps-mix", clumps(3000, 40, 77, a0=0.01), 0.02, 2))
+    out.append(("clumps-mix-m5", clumps(3000, 40, 78, a0=0.01), 0.03, 5))
+    return out
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
+def test_oracle_matches_brute(case):
+    name, p, eps, minpts = case
+    want = brute.dbscan(p, eps, minpts)
+    got = oracle.dbscan(p, eps, minpts)
+    assert np.array_equal(got, want), name
+    assert np.array_equal(oracle.core_flags(p, eps, minpts), brute.core_flags(p, eps, minpts))
+    assert oracle.pair_count(p, eps) == brute.pair_count(p, eps)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_fof_equals_components(seed):
+    """minPts = 2: labels are the connected components of the eps-graph, isolated
+    points noise (subsection "Initial DBSCAN implementation")."""
+    p = clumps(4000, 30, 900 + seed, a0=0.01)
+    eps = 0.015
+    assert np.array_equal(oracle.dbscan(p, eps, 2), brute.fof_components(p, eps))
+
+
+@pytest.mark.slow
+def test_c1_full_bruteforce():
+    """The whole C1 configuration (32,768 uniform points, FoF) against the
+    connected components of the brute-force eps-graph."""
+    cfg = CONFIGS["C1"]
+    p = cfg.points()
+    got = oracle.dbscan(p, cfg.eps, cfg.minpts)
+    want = brute.fof_components(p, cfg.eps)
+    assert np.array_equal(got, want)
+    assert (got >= 0).sum() > 0
+
+
+# ---- invariants ------------------------------------------------------------------
+
+def _check_invariants(p, eps, minpts, lab):
+    n = len(p)
+    idx = np.arange(n)
+    cl = lab >= 0
+    assert np.all(lab[cl] <= idx[cl])                 # id = smallest member
+    assert np.all(lab[lab[cl]] == lab[cl])            # the id point is in its cluster
+    core = brute.core_flags(p, eps, minpts)
+    assert np.all(cl[core])                           # every core point is clustered
+    nb = brute.neighbour_lists(p, eps)
+    for i in np.nonzero(~cl)[0]:                      # noise touches no core point
+        assert not core[nb[i]].any()
+    for i in np.nonzero(core)[0]:                     # core neighbours share a cluster
+        cn = nb[i][core[nb[i]]]
+        assert np.all(lab[cn] == lab[i])
+
+
+@pytest.mark.parametrize("minpts", [2, 4, 8])
+def test_invariants(minpts):
+    p = _clumpy(np.random.default_rng(minpts), 1500, 10, 0.02)
+    eps = 0.03
+    _check_invariants(p, eps, minpts, oracle.dbscan(p, eps, minpts))
+
+
+def _canonical(lab):
+    """Partition as a set of frozensets (noise kept apart)."""
+    groups = {}
+    for i, l in enumerate(lab):
+        groups.setdefault(int(l), set()).add(i)
+    noise = frozenset(groups.pop(-1, set()))
+    return noise, frozenset(frozenset(g) for g in groups.values())
+
+
+@pytest.mark.parametrize("minpts", [2, 5])
+def test_permutation_invariance(minpts):
+    """FoF/core classification does not depend on input order; for minPts = 2
+    the whole partition does not (for minPts > 2 a border point's choice can
+    legitimately follow the indices, so only cores are compared there)."""
+    rng = np.random.default_rng(5)
+    p = _clumpy(rng, 1200, 8, 0.02)
+    eps = 0.03
+    perm = rng.permutation(len(p))
+    a = oracle.dbscan(p, eps, minpts)
+    b = oracle.dbscan(p[perm], eps, minpts)
+    back = np.empty_like(b)
+    back[perm] = b
+    # map labels of the permuted run back to original indices of the id point
+    relab = np.where(back >= 0, perm[np.clip(back, 0, None)], -1)
+    if minpts == 2:
+        assert _canonical(a) == _canonical(relab)
+    else:
+        core = oracle.core_flags(p, eps, minpts)
+        assert _canonical(np.where(core, a, -1)) == _canonical(np.where(core, relab, -1))
+
+
+@pytest.mark.parametrize("k", [-3, 2, 5])
+def test_power_of_two_scaling(k):
+    """Scaling coordinates and eps by 2^k is exact in FP32 (no overflow or
+    underflow here), so the labels are identical."""
+    p = _clumpy(np.random.default_rng(9), 1000, 6, 0.02)
+    eps = 0.03
+    s = np.float32(2.0 ** k)
+    assert np.array_equal(oracle.dbscan(p, eps, 3), oracle.dbscan(p * s, eps * float(s), 3))
+
+
+def test_exact_translation():
+    """Translating points on a 2^-10 lattice by a multiple of 2^-10 keeps every
+    difference exact, hence identical labels."""
+    rng = np.random.default_rng(4)
+    p = (rng.integers(0, 1024, (1500, 3)) / 1024.0).astype(np.float32)
+    q = (p + np.float32(37 / 1024.0)).astype(np.float32)
+    assert np.array_equal(q - np.float32(37 / 1024.0), p)
+    eps = 0.02
+    assert np.array_equal(oracle.dbscan(p, eps, 3), oracle.dbscan(q, eps, 3))
+
+
+# ---- argument checking ---------------------------------------------------------------
+
+def test_errors():
+    p = np.zeros((4, 3), np.float32)
+    with pytest.raises(oracle.OracleError):
+        oracle.dbscan(p, -1.0, 2)
+    with pytest.raises(oracle.OracleError):
+        oracle.dbscan(p, float("nan"), 2)
+    with pytest.raises(oracle.OracleError):
+        oracle.dbscan(p, 0.1, 0)
+    q = p.copy()
+    q[2, 1] = np.inf
+    with pytest.raises(oracle.OracleError):
+        oracle.dbscan(q, 0.1, 2)
+    assert oracle.dbscan(np.zeros((0, 3), np.float32), 0.1, 2).shape == (0,)
+
+
+# ---- planted mistakes: the pins must catch each one -------------------------------
+
+MUTATIONS = [
+    ("open neighbourhood", "return d2 <= e2;", "return d2 < e2;"),
+    ("dropped z term", "d2 = d2 + dz * dz;", "d2 = d2 + 0.0f * dz;"),
+    ("wrong sign in dy", "float dy = p[1] - q[1];", "float dy = p[1] + q[1];"),
+    ("row offset off by one", "int64_t y = cy + (r % 3) - 1;", "int64_t y = cy + (r % 3);"),
+    ("cell too small", "H *= 1.0 + ldexp(1.0, -10);", "H *= 0.5;"),
+    ("core strict", "st.core[i] = st.count[i] >= minpts;", "st.core[i] = st.count[i] > minpts;"),
+    ("border takes the largest K", "if (st->border[i] < 0 || k < st->border[i])",
+     "if (st->border[i] < 0 || k > st->border[i])"),
+    ("root is the larger index", "    if (a < b)\n        parent[b] = a;",
+     "    if (a > b)\n        parent[b] = a;"),
+    ("union of core with non-core", "if (j > i && st->core[j])", "if (j > i)"),
+    ("border id ignored", "if (!st.core[i] && st.border[i] >= 0 && (int32_t)i < id[st.border[i]])",
+     "if (0)"),
+]
+
+
+def _pins_pass(lib_dbscan) -> bool:
+    for name, p, eps, minpts, want in golden_cases():
+        if not np.array_equal(lib_dbscan(p, eps, minpts), want):
+            return False
+    for name, p, eps, minpts in _cases()[:12]:
+        if not np.array_equal(lib_dbscan(p, eps, minpts), brute.dbscan(p, eps, minpts)):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("mut", MUTATIONS, ids=lambda m: m[0])
+def test_planted_mistake_is_caught(mut, tmp_path):
+    import ctypes
+    name, old, new = mut
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "dbscan_oracle.c")).read()
+    assert src.count(old) == 1, f"mutation anchor not found: {name}"
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", *oracle.CFLAGS, "-o", str(so), str(path), "-lm"], check=True)
+    lib = ctypes.CDLL(str(so))
+    lib.oracle_dbscan.restype = ctypes.c_int
+    lib.oracle_dbscan.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_float, ctypes.c_int32,
+                                  ctypes.c_void_p]
+
+    def run(p, eps, minpts):
+        p = np.ascontiguousarray(p, np.float32)
+        lab = np.empty(len(p), np.int32)
+        rc = lib.oracle_dbscan(p.ctypes.data, len(p), float(np.float32(eps)), minpts, lab.ctypes.data)
+        return lab if rc == 0 else None
+
+    assert not _pins_pass(run), f"planted mistake not caught: {name}"
