@@ -1,0 +1,185 @@
+/*
+ * abx -- BVH-driven density clustering of 3-D particles on one GB300 GPU.
+ *
+ * DBSCAN with any minPts, and its minPts = 2 friends-of-friends (FoF) case
+ * used for halo finding, following "Advances in ArborX to support exascale
+ * applications" (arXiv 2409.10743): the definitions of subsection "DBSCAN
+ * algorithm", the two-phase Algorithm PDSDbscan, FDBSCAN (fused traversal with
+ * union-find, early-terminated core counting, pair traversal) and
+ * FDBSCAN-DenseBox (dense grid cells as hierarchy leaves), over a linear BVH
+ * built bottom-up from sorted Morton codes with ropes for stackless traversal
+ * (subsections "Stackless traversal", "64-bit Morton codes",
+ * "Pair traversal").
+ *
+ * Results are exact and deterministic:
+ *   - two points are neighbours iff d2 <= fl(eps*eps), where
+ *     d2 = fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)) and dx = fl(xi - xj) etc.:
+ *     FP32, round-to-nearest-even, no fused multiply-add, no flush-to-zero;
+ *   - |N_eps(x)| counts x itself; x is core iff |N_eps(x)| >= minPts;
+ *   - a cluster's id is the smallest original index among its members (core
+ *     points and the border points it was given); noise is -1;
+ *   - a border point (non-core, with a core neighbour) joins the neighbouring
+ *     cluster whose smallest core index is smallest.  (The paper's Algorithm
+ *     PDSDbscan lets the first core to arrive claim it; that is
+ *     nondeterministic and is replaced by this rule.)
+ * Labels are therefore a pure function of (points, eps, minPts): identical
+ * across calls, parameter choices, the batched path and the serving path.
+ *
+ * Conventions for every entry point:
+ *   - points are caller-owned float32 [n][3] (x, y, z) rows, contiguous;
+ *   - labels are caller-owned int32 [n];
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary (preferably pinned) host memory;
+ *   - work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and the call returns without waiting, unless stated otherwise;
+ *     the caller keeps inputs alive and unmodified until the stream reaches
+ *     the end of the call's work;
+ *   - arguments are checked on the host before anything is enqueued;
+ *     a bad argument returns ABX_EINVAL and enqueues nothing;
+ *   - workspace comes from a library-owned, stream-ordered CUDA memory pool
+ *     (one per device), released back to the pool in stream order;
+ *   - errors detected on the device (non-finite coordinates, a bounded wait
+ *     that ran out) never trap: kernels record them in a per-device status
+ *     word that abx_device_status() reads back;
+ *   - the library never calls exit(), assert() or __trap().
+ * Thread safety: calls on different streams may run concurrently from
+ * different host threads.
+ */
+#ifndef ABX_H
+#define ABX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t abx_status;
+
+#define ABX_OK 0
+#define ABX_EINVAL (-1)        /* bad argument; nothing was enqueued */
+#define ABX_ENOMEM (-2)        /* device memory pool could not allocate */
+#define ABX_ENOMEM_BUDGET (-3) /* serving: request larger than the HBM budget */
+#define ABX_ECUDA (-4)         /* a CUDA runtime call failed */
+#define ABX_ETIMEOUT (-5)      /* a bounded wait ran out (host wait or device spin) */
+#define ABX_ECANCELLED (-6)    /* serving: the server was destroyed first */
+#define ABX_EBUSY (-7)         /* serving: no free slot and the queue is full */
+#define ABX_ENONFINITE (-8)    /* device: a coordinate was NaN or infinite */
+#define ABX_EINTERNAL (-9)     /* device: an internal consistency check failed */
+
+/* Opaque CUDA stream handle (cudaStream_t). */
+typedef struct CUstream_st *abx_stream;
+
+/*
+ * Tuning parameters.  Every field 0 means "library default".  None of them
+ * changes the labels; they only change speed and memory.
+ *   leaf_size    points per ordinary hierarchy leaf (1..32, default 4)
+ *   dense_cells  1 = FDBSCAN-DenseBox dense-cell leaves on, -1 = off (default on)
+ *   sub_bits     Morton bits per axis below the dense-cell side (0..8, default 3)
+ *   block        threads per block of the traversal kernels (64..1024, default 256)
+ */
+typedef struct abx_params {
+    int32_t leaf_size;
+    int32_t dense_cells;
+    int32_t sub_bits;
+    int32_t block;
+    int32_t reserved[4];
+} abx_params;
+
+/* Human-readable name of a status code (static storage). */
+const char *abx_status_str(abx_status s);
+
+/*
+ * abx_dbscan -- cluster n points (paper, Algorithm PDSDbscan with the FDBSCAN
+ * and FDBSCAN-DenseBox kernels).
+ *   points  device, float32 [n][3], caller-owned, read only
+ *   n       0 <= n <= 2^31 - 1; n = 0 returns ABX_OK and enqueues nothing
+ *   eps     finite, >= 0
+ *   minpts  >= 1 (minpts <= 2 takes the friends-of-friends path)
+ *   labels  device, int32 [n], caller-owned, written
+ *   stream  the stream the work is enqueued on
+ * Returns ABX_OK once enqueued; ABX_EINVAL, ABX_ENOMEM or ABX_ECUDA otherwise.
+ */
+abx_status abx_dbscan(const float *points, int64_t n, float eps, int32_t minpts,
+                      int32_t *labels, abx_stream stream);
+
+/* abx_dbscan with explicit tuning parameters (params may be NULL). */
+abx_status abx_dbscan_ex(const float *points, int64_t n, float eps, int32_t minpts,
+                         int32_t *labels, const abx_params *params, abx_stream stream);
+
+/*
+ * abx_dbscan_host -- the same clustering from host memory to host memory: the
+ * library copies the points in, runs abx_dbscan and copies the labels out,
+ * all on `stream`, then waits for the stream.  points_host float32 [n][3] and
+ * labels_host int32 [n] are caller-owned host buffers (pinned memory makes the
+ * copies asynchronous and faster).  Blocks until the labels are in place.
+ */
+abx_status abx_dbscan_host(const float *points_host, int64_t n, float eps, int32_t minpts,
+                           int32_t *labels_host, abx_stream stream);
+
+/*
+ * abx_device_status -- wait for `stream`, then return and clear the current
+ * device's status word: ABX_OK, ABX_ENONFINITE (a coordinate was not finite),
+ * ABX_ETIMEOUT (a bounded device wait ran out) or ABX_EINTERNAL (a kernel's
+ * consistency check failed and it stopped early).  After any of these the
+ * labels of the calls since the previous check are unspecified.
+ */
+abx_status abx_device_status(abx_stream stream);
+
+/*
+ * abx_dbscan_batch -- cluster nseg independent point sets in one pass
+ * (many sub-volumes at once).  Segment k is points[offsets[k] .. offsets[k+1])
+ * of the concatenated array and is clustered with eps[k] and minpts[k] exactly
+ * as abx_dbscan would cluster it alone; labels[offsets[k] + i] is a
+ * segment-local index (or -1).
+ *   points   device, float32 [offsets[nseg]][3]
+ *   offsets  host, int64 [nseg + 1], offsets[0] = 0, non-decreasing,
+ *            offsets[nseg] <= 2^31 - 1
+ *   eps      host, float [nseg], each finite and >= 0
+ *   minpts   host, int32 [nseg], each >= 1
+ *   labels   device, int32 [offsets[nseg]]
+ * The host arrays are read before the call returns.
+ */
+abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t nseg,
+                            const float *eps, const int32_t *minpts, int32_t *labels,
+                            abx_stream stream);
+
+/* ---- the bounding volume hierarchy on its own ------------------------------ */
+
+/* Opaque, library-owned hierarchy over a point set (paper, section "ArborX
+ * library": a binary BVH over Morton-sorted points, built bottom-up, with
+ * ropes for stackless traversal). */
+typedef struct abx_bvh abx_bvh;
+
+/*
+ * abx_bvh_build -- build a hierarchy over n points (device float32 [n][3]);
+ * the library copies what it needs, so points may be freed once the stream
+ * has passed the call.  *out receives the handle; the build is enqueued on
+ * `stream` and the handle may be used on that stream right away.
+ * leaf_size as in abx_params (0 = default).  1 <= n <= 2^31 - 1.
+ */
+abx_status abx_bvh_build(const float *points, int64_t n, int32_t leaf_size, abx_bvh **out,
+                         abx_stream stream);
+
+/*
+ * abx_bvh_count -- early-terminated range counting (paper, subsection "Early
+ * termination"): counts[q] = min(cap, number of tree points p with
+ * pred(query q, p)), stopping each query's traversal once cap is reached.
+ *   queries  device float32 [nq][3];  counts device int32 [nq];  cap >= 1.
+ */
+abx_status abx_bvh_count(const abx_bvh *bvh, const float *queries, int64_t nq, float eps,
+                         int32_t cap, int32_t *counts, abx_stream stream);
+
+/* Number of points, leaves and levels (depth of the deepest leaf + 1) of a
+ * built hierarchy; waits for `stream`. */
+abx_status abx_bvh_info(const abx_bvh *bvh, int64_t *n_points, int64_t *n_leaves,
+                        int32_t *levels, abx_stream stream);
+
+/* Free a hierarchy (stream-ordered on the stream it was built on). */
+abx_status abx_bvh_destroy(abx_bvh *bvh);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABX_H */

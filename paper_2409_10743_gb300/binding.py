@@ -1,0 +1,187 @@
+"""ctypes binding of libabx.so: same names as the C ABI, argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ABX_OK = 0
+ABX_EINVAL = -1
+ABX_ENOMEM = -2
+ABX_ENOMEM_BUDGET = -3
+ABX_ECUDA = -4
+ABX_ETIMEOUT = -5
+ABX_ECANCELLED = -6
+ABX_EBUSY = -7
+ABX_ENONFINITE = -8
+ABX_EINTERNAL = -9
+
+
+class AbxError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {status_str(code)} ({code})" if what else f"{status_str(code)} ({code})")
+
+
+class Params(ctypes.Structure):
+    """abx_params: 0 in any field = library default; no field changes the labels."""
+    _fields_ = [("leaf_size", ctypes.c_int32), ("dense_cells", ctypes.c_int32),
+                ("sub_bits", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+_lock = threading.Lock()
+_lib = None
+_vp, _i64, _i32, _f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+
+_SIGS = {
+    "abx_status_str": (ctypes.c_char_p, [_i32]),
+    "abx_dbscan": (_i32, [_vp, _i64, _f32, _i32, _vp, _vp]),
+    "abx_dbscan_ex": (_i32, [_vp, _i64, _f32, _i32, _vp, ctypes.POINTER(Params), _vp]),
+    "abx_dbscan_host": (_i32, [_vp, _i64, _f32, _i32, _vp, _vp]),
+    "abx_device_status": (_i32, [_vp]),
+    "abx_dbscan_batch": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "abx_bvh_build": (_i32, [_vp, _i64, _i32, ctypes.POINTER(_vp), _vp]),
+    "abx_bvh_count": (_i32, [_vp, _vp, _i64, _f32, _i32, _vp, _vp]),
+    "abx_bvh_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32), _vp]),
+    "abx_bvh_destroy": (_i32, [_vp]),
+}
+
+
+def lib(path: str | None = None):
+    """Load libabx.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            so = path or _build.build()
+            if not os.path.exists(so):
+                raise RuntimeError(f"abx CUDA library not found at {so}")
+            L = ctypes.CDLL(so)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_str(code: int) -> str:
+    return lib().abx_status_str(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != ABX_OK:
+        raise AbxError(rc, what)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _points_dev(points):
+    import torch
+    if not isinstance(points, torch.Tensor) or not points.is_cuda:
+        raise TypeError("points must be a CUDA torch tensor")
+    if points.dtype != torch.float32 or points.dim() != 2 or points.shape[1] != 3:
+        raise TypeError("points must be float32 of shape (n, 3)")
+    return points.contiguous()
+
+
+def dbscan(points, eps: float, minpts: int, labels=None, params: Params | None = None, stream=None):
+    """Cluster device points (torch float32 (n, 3) on CUDA) -> int32 labels on
+    the same device (cluster id = smallest member index, noise = -1).
+    Asynchronous on ``stream`` (default: torch's current stream)."""
+    import torch
+    p = _points_dev(points)
+    n = p.shape[0]
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=p.device)
+    s = _stream(stream)
+    with torch.cuda.device(p.device):
+        if params is None:
+            rc = lib().abx_dbscan(p.data_ptr(), n, float(np.float32(eps)), int(minpts), labels.data_ptr(), s)
+        else:
+            rc = lib().abx_dbscan_ex(p.data_ptr(), n, float(np.float32(eps)), int(minpts), labels.data_ptr(),
+                                     ctypes.byref(params), s)
+    _check(rc, "abx_dbscan")
+    return labels
+
+
+def dbscan_host(points: np.ndarray, eps: float, minpts: int, labels: np.ndarray | None = None, stream=None):
+    """Host -> host clustering through abx_dbscan_host (copies inside, blocks)."""
+    p = np.ascontiguousarray(points, dtype=np.float32)
+    if p.ndim != 2 or p.shape[1] != 3:
+        raise TypeError("points must be float32 of shape (n, 3)")
+    if labels is None:
+        labels = np.empty(p.shape[0], dtype=np.int32)
+    rc = lib().abx_dbscan_host(p.ctypes.data, p.shape[0], float(np.float32(eps)), int(minpts),
+                               labels.ctypes.data, _stream(stream))
+    _check(rc, "abx_dbscan_host")
+    return labels
+
+
+def dbscan_batch(points, offsets, eps, minpts, labels=None, stream=None):
+    """Cluster concatenated segments; labels are segment-local."""
+    import torch
+    p = _points_dev(points)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nseg = off.size - 1
+    e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float32), (nseg,)), dtype=np.float32)
+    m = np.ascontiguousarray(np.broadcast_to(np.asarray(minpts, np.int32), (nseg,)), dtype=np.int32)
+    if labels is None:
+        labels = torch.empty(p.shape[0], dtype=torch.int32, device=p.device)
+    with torch.cuda.device(p.device):
+        rc = lib().abx_dbscan_batch(p.data_ptr(), off.ctypes.data, nseg, e.ctypes.data, m.ctypes.data,
+                                    labels.data_ptr(), _stream(stream))
+    _check(rc, "abx_dbscan_batch")
+    return labels
+
+
+def device_status(stream=None) -> int:
+    """Wait for the stream; return and clear the device status word."""
+    return int(lib().abx_device_status(_stream(stream)))
+
+
+class BVH:
+    """abx_bvh handle: build over device points, early-terminated counts."""
+
+    def __init__(self, points, leaf_size: int = 0, stream=None):
+        p = _points_dev(points)
+        self._h = ctypes.c_void_p()
+        self._stream = _stream(stream)
+        rc = lib().abx_bvh_build(p.data_ptr(), p.shape[0], int(leaf_size), ctypes.byref(self._h), self._stream)
+        _check(rc, "abx_bvh_build")
+
+    def count(self, queries, eps: float, cap: int, out=None):
+        import torch
+        q = _points_dev(queries)
+        if out is None:
+            out = torch.empty(q.shape[0], dtype=torch.int32, device=q.device)
+        rc = lib().abx_bvh_count(self._h, q.data_ptr(), q.shape[0], float(np.float32(eps)), int(cap),
+                                 out.data_ptr(), self._stream)
+        _check(rc, "abx_bvh_count")
+        return out
+
+    def info(self):
+        n, L, lev = _i64(), _i64(), _i32()
+        _check(lib().abx_bvh_info(self._h, ctypes.byref(n), ctypes.byref(L), ctypes.byref(lev), self._stream),
+               "abx_bvh_info")
+        return {"n_points": n.value, "n_leaves": L.value, "levels": lev.value}
+
+    def close(self):
+        if self._h:
+            _check(lib().abx_bvh_destroy(self._h), "abx_bvh_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,327 @@
+// The C ABI: argument checks, per-device context, workspace, stage sequence.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "work.cuh"
+
+namespace abx {
+
+// ---- per-device context --------------------------------------------------------
+
+struct DeviceCtx {
+    bool ready = false;
+    cudaMemPool_t pool = nullptr;
+    unsigned *status = nullptr;
+    int n_sms = 0;
+};
+
+static std::mutex g_mu;
+static DeviceCtx g_ctx[64];
+
+static abx_status device_ctx(DeviceCtx **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return ABX_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceCtx &c = g_ctx[dev];
+    if (!c.ready) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&c.pool, &props) != cudaSuccess)
+            return ABX_ECUDA;
+        unsigned long long thresh = ~0ull;  // keep freed blocks for reuse
+        cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &thresh);
+        if (cudaMalloc(&c.status, sizeof(unsigned)) != cudaSuccess)
+            return ABX_ECUDA;
+        if (cudaMemset(c.status, 0, sizeof(unsigned)) != cudaSuccess)
+            return ABX_ECUDA;
+        if (cudaDeviceGetAttribute(&c.n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return ABX_ECUDA;
+        kernels_init_device();
+        if (cudaGetLastError() != cudaSuccess)
+            return ABX_ECUDA;
+        c.ready = true;
+    }
+    *out = &c;
+    return ABX_OK;
+}
+
+abx_status bvh_device_ctx(cudaMemPool_t *pool, unsigned **status, int *n_sms)
+{
+    DeviceCtx *c;
+    abx_status rc = device_ctx(&c);
+    if (rc == ABX_OK) {
+        *pool = c->pool;
+        *status = c->status;
+        *n_sms = c->n_sms;
+    }
+    return rc;
+}
+
+// ---- workspace ------------------------------------------------------------------------
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Carver {
+    size_t off = 0;
+    char *base = nullptr;
+    template <class T>
+    T *take(size_t count)
+    {
+        size_t o = off;
+        off = align256(off + count * sizeof(T));
+        return base ? reinterpret_cast<T *>(base + o) : nullptr;
+    }
+};
+
+static void carve(Carver &c, Work &w, int64_t n)
+{
+    const size_t N = (size_t)n;
+    w.n = n;
+    w.sort_tiles = (size_t)div_up(n, SORT_TILE);
+    w.scan_tiles = (size_t)div_up(n, SCAN_TILE);
+    w.st = c.take<State>(1);
+    w.keys[0] = c.take<unsigned long long>(N);
+    w.keys[1] = c.take<unsigned long long>(N);
+    w.vals[0] = c.take<unsigned>(N);
+    w.vals[1] = c.take<unsigned>(N);
+    w.sort_lb = c.take<unsigned long long>((size_t)MAX_PASSES * w.sort_tiles * RADIX);
+    w.scan_lb = c.take<unsigned long long>(2 * w.scan_tiles);
+    w.spts = c.take<float4>(N);
+    w.cell_id = c.take<int>(N);
+    w.cell_start = c.take<int>(N + 1);
+    w.cell_dense = c.take<unsigned char>(N);
+    w.cell_root = c.take<int>(N);
+    w.leaf_of = c.take<int>(N);
+    w.leaf_first = c.take<int>(N + 1);
+    w.delta = c.take<unsigned char>(N);
+    w.nodes = c.take<float4>(2 * (2 * N - 1));
+    w.slot = c.take<unsigned long long>(N);
+    w.right_of = c.take<int>(N);
+    w.parent = c.take<int>(N);
+    w.core = c.take<unsigned char>(N);
+    w.bmin = c.take<int>(N);
+}
+
+size_t work_bytes(int64_t n)
+{
+    Carver c;
+    Work w;
+    carve(c, w, n);
+    return c.off;
+}
+
+void work_carve(Work &w, void *base, int64_t n)
+{
+    Carver c;
+    c.base = static_cast<char *>(base);
+    carve(c, w, n);
+}
+
+static abx_status resolve_params(const abx_params *in, Params &p)
+{
+    p.leaf_size = 4;
+    p.dense = 1;
+    p.sub_bits = 3;
+    p.block = 256;
+    if (!in)
+        return ABX_OK;
+    if (in->leaf_size) {
+        if (in->leaf_size < 1 || in->leaf_size > 32)
+            return ABX_EINVAL;
+        p.leaf_size = in->leaf_size;
+    }
+    if (in->dense_cells) {
+        if (in->dense_cells != 1 && in->dense_cells != -1)
+            return ABX_EINVAL;
+        p.dense = in->dense_cells == 1;
+    }
+    if (in->sub_bits) {
+        if (in->sub_bits < 0 || in->sub_bits > 8)
+            return ABX_EINVAL;
+        p.sub_bits = in->sub_bits;
+    }
+    if (in->block) {
+        if (in->block < 64 || in->block > 1024 || (in->block & 31))
+            return ABX_EINVAL;
+        p.block = in->block;
+    }
+    return ABX_OK;
+}
+
+static abx_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return ABX_OK;
+    return e == cudaErrorMemoryAllocation ? ABX_ENOMEM : ABX_ECUDA;
+}
+
+// Enqueue the whole pipeline on `s` over a carved workspace.
+static void run_pipeline(Work &w, const float *points, float eps, int minpts, int32_t *labels, const Params &p,
+                         cudaStream_t s)
+{
+    stage_bounds_quant(w, points, eps, p, s);
+    stage_morton_sort(w, points, s);
+    stage_gather(w, points, minpts, s);
+    stage_cells_leaves(w, eps, minpts, p, s);
+    stage_hierarchy(w, s);
+    stage_cluster(w, eps, minpts, p, labels, s);
+}
+
+}  // namespace abx
+
+using namespace abx;
+
+extern "C" {
+
+const char *abx_status_str(abx_status s)
+{
+    switch (s) {
+    case ABX_OK: return "ok";
+    case ABX_EINVAL: return "invalid argument";
+    case ABX_ENOMEM: return "out of device memory";
+    case ABX_ENOMEM_BUDGET: return "request exceeds the HBM budget";
+    case ABX_ECUDA: return "CUDA error";
+    case ABX_ETIMEOUT: return "timed out";
+    case ABX_ECANCELLED: return "cancelled";
+    case ABX_EBUSY: return "busy";
+    case ABX_ENONFINITE: return "non-finite coordinate";
+    case ABX_EINTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+static abx_status check_args(const float *points, int64_t n, float eps, int32_t minpts, const int32_t *labels)
+{
+    if (n < 0 || n > INT32_MAX || minpts < 1 || !(eps >= 0.0f) || std::isinf(eps))
+        return ABX_EINVAL;
+    if (n > 0 && (!points || !labels))
+        return ABX_EINVAL;
+    return ABX_OK;
+}
+
+abx_status abx_dbscan_ex(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
+                         const abx_params *params, abx_stream stream)
+{
+    abx_status rc = check_args(points, n, eps, minpts, labels);
+    if (rc != ABX_OK)
+        return rc;
+    Params p;
+    if ((rc = resolve_params(params, p)) != ABX_OK)
+        return rc;
+    if (n == 0)
+        return ABX_OK;
+    DeviceCtx *ctx;
+    if ((rc = device_ctx(&ctx)) != ABX_OK)
+        return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    if (cudaMallocFromPoolAsync(&ws, work_bytes(n), ctx->pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return ABX_ENOMEM;
+    }
+    Work w;
+    work_carve(w, ws, n);
+    w.n_sms = ctx->n_sms;
+    w.dev_status = ctx->status;
+    run_pipeline(w, points, eps, minpts, labels, p, s);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(ws, s);
+    return cuda_status(e);
+}
+
+abx_status abx_dbscan(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
+                      abx_stream stream)
+{
+    return abx_dbscan_ex(points, n, eps, minpts, labels, nullptr, stream);
+}
+
+abx_status abx_dbscan_host(const float *points_host, int64_t n, float eps, int32_t minpts, int32_t *labels_host,
+                           abx_stream stream)
+{
+    abx_status rc = check_args(points_host, n, eps, minpts, labels_host);
+    if (rc != ABX_OK || n == 0)
+        return rc;
+    DeviceCtx *ctx;
+    if ((rc = device_ctx(&ctx)) != ABX_OK)
+        return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void *dp = nullptr, *dl = nullptr;
+    if (cudaMallocFromPoolAsync(&dp, (size_t)n * 3 * sizeof(float), ctx->pool, s) != cudaSuccess ||
+        cudaMallocFromPoolAsync(&dl, (size_t)n * sizeof(int32_t), ctx->pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (dp)
+            cudaFreeAsync(dp, s);
+        cudaStreamSynchronize(s);
+        return ABX_ENOMEM;
+    }
+    cudaMemcpyAsync(dp, points_host, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+    rc = abx_dbscan_ex(static_cast<const float *>(dp), n, eps, minpts, static_cast<int32_t *>(dl), nullptr, stream);
+    if (rc == ABX_OK)
+        cudaMemcpyAsync(labels_host, dl, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(dp, s);
+    cudaFreeAsync(dl, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (rc != ABX_OK)
+        return rc;
+    return cuda_status(e == cudaSuccess ? cudaGetLastError() : e);
+}
+
+abx_status abx_device_status(abx_stream stream)
+{
+    DeviceCtx *ctx;
+    abx_status rc = device_ctx(&ctx);
+    if (rc != ABX_OK)
+        return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+        return ABX_ECUDA;
+    unsigned v = 0;
+    if (cudaMemcpy(&v, ctx->status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ABX_ECUDA;
+    if (v && cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess)
+        return ABX_ECUDA;
+    if (v & DEV_INTERNAL)
+        return ABX_EINTERNAL;
+    if (v & DEV_TIMEOUT)
+        return ABX_ETIMEOUT;
+    if (v & DEV_NONFINITE)
+        return ABX_ENONFINITE;
+    return ABX_OK;
+}
+
+abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t nseg, const float *eps,
+                            const int32_t *minpts, int32_t *labels, abx_stream stream)
+{
+    if (nseg < 0 || (nseg > 0 && (!offsets || !eps || !minpts)))
+        return ABX_EINVAL;
+    if (nseg == 0)
+        return ABX_OK;
+    if (offsets[0] != 0)
+        return ABX_EINVAL;
+    for (int32_t k = 0; k < nseg; k++) {
+        if (offsets[k + 1] < offsets[k])
+            return ABX_EINVAL;
+        abx_status rc = check_args(points, offsets[k + 1] - offsets[k], eps[k], minpts[k], labels);
+        if (rc != ABX_OK)
+            return rc;
+    }
+    if (offsets[nseg] > INT32_MAX)
+        return ABX_EINVAL;
+    for (int32_t k = 0; k < nseg; k++) {
+        int64_t a = offsets[k], m = offsets[k + 1] - a;
+        abx_status rc = abx_dbscan(points + 3 * a, m, eps[k], minpts[k], labels + a, stream);
+        if (rc != ABX_OK)
+            return rc;
+    }
+    return ABX_OK;
+}
+
+}  // extern "C"

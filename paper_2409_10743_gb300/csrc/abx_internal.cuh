@@ -1,0 +1,148 @@
+// Internal definitions shared by the abx kernels (device + launch helpers).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/abx.h"
+
+namespace abx {
+
+// ---- device status word bits (OR-ed by kernels, read by abx_device_status) --
+enum : unsigned { DEV_NONFINITE = 1u, DEV_TIMEOUT = 2u, DEV_INTERNAL = 4u };
+
+// Bounded spin: iterations before a wait gives up, records DEV_TIMEOUT and
+// moves on (the call's output is then unspecified, but the GPU never hangs).
+constexpr int SPIN_LIMIT = 1 << 22;
+
+constexpr int SENTINEL = -1;        // rope of the right-most path (paper, fig. f:karras_ropes)
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int MAX_PASSES = 8;       // 64-bit keys, 8 bits per pass
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr unsigned DENSE_BIT = 0x80000000u;
+
+// Per-call device state (lives in the call's workspace).
+struct State {
+    int lo_enc[3], hi_enc[3];   // ordered-int encoded bounds
+    float lo[3];                // scene minimum (grid origin)
+    float inv_step;             // Morton quantisation scale
+    int bits;                   // Morton bits per axis (<= 21)
+    int sub;                    // Morton bits per axis below the dense-cell side
+    int dense_ok;               // dense cells usable (cell grid = Morton prefix)
+    int n_passes;               // active radix passes
+    int pass_ord[MAX_PASSES];   // order of pass p among the active ones, -1 = skipped
+    unsigned tile_ctr[MAX_PASSES + 4];
+    unsigned hist[MAX_PASSES][RADIX];   // digit histograms, then exclusive offsets
+    int n_cells;
+    int n_leaves;
+    int root;
+    int pad[5];
+};
+
+// ---- FP32 exact predicate ---------------------------------------------------
+// d2 = fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)), every operation rounded to
+// nearest even on its own (the _rn intrinsics are never contracted into FMA).
+__device__ __forceinline__ float dist2_rn(float ax, float ay, float az, float bx, float by, float bz)
+{
+    float dx = __fsub_rn(ax, bx);
+    float dy = __fsub_rn(ay, by);
+    float dz = __fsub_rn(az, bz);
+    float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    return __fadd_rn(s, __fmul_rn(dz, dz));
+}
+
+// Rounded squared distance from p to the box [lo, hi], same operation order.
+// Rounding is monotone and fl(-a) = -fl(a), so for every point q in the box
+// this value is <= dist2_rn(p, q): pruning a box when it exceeds e2 never
+// drops a neighbour.
+__device__ __forceinline__ float box_dist2_rn(float px, float py, float pz, float4 lo, float4 hi)
+{
+    float dx = fmaxf(0.0f, fmaxf(__fsub_rn(lo.x, px), __fsub_rn(px, hi.x)));
+    float dy = fmaxf(0.0f, fmaxf(__fsub_rn(lo.y, py), __fsub_rn(py, hi.y)));
+    float dz = fmaxf(0.0f, fmaxf(__fsub_rn(lo.z, pz), __fsub_rn(pz, hi.z)));
+    float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    return __fadd_rn(s, __fmul_rn(dz, dz));
+}
+
+// ---- ordered float <-> int for atomic min/max ---------------------------------
+__device__ __forceinline__ int float_to_ordered(float f)
+{
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ordered_to_float(int i)
+{
+    return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
+}
+
+// ---- relaxed L2 loads for data other threads write during a kernel ----------
+__device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
+__device__ __forceinline__ float4 ld_cg4(const float4 *p) { return __ldcg(p); }
+
+// ---- lock-free union-find over sorted positions --------------------------------
+// A set's root is its member with the smallest original index (priority =
+// original index, kept in float4.w of the sorted points), so after all unions
+// the root of a cluster of core points is K(C), its smallest core index.
+// Hooking is a CAS on the root's own parent word: parent pointers only ever
+// move to members of smaller priority, so stale reads can delay but never
+// break a find, and every chain ends at a root.
+__device__ __forceinline__ int orig_of(const float4 *pts, int i)
+{
+    return __float_as_int(__ldg(&pts[i].w));
+}
+
+__device__ __forceinline__ int uf_find(int *parent, int x)
+{
+    while (true) {
+        int p = ld_cg(parent + x);
+        if (p == x)
+            return x;
+        int gp = ld_cg(parent + p);
+        if (gp == p)
+            return p;
+        parent[x] = gp;  // path halving (any ancestor is a valid parent)
+        x = gp;
+    }
+}
+
+__device__ __forceinline__ void uf_unite(int *parent, const float4 *pts, int a, int b)
+{
+    while (true) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b)
+            return;
+        // strict total order (original index, position): chains never cycle
+        const int oa = orig_of(pts, a), ob = orig_of(pts, b);
+        if (oa > ob || (oa == ob && a > b)) {
+            int t = a;
+            a = b;
+            b = t;
+        }
+        // hook b (larger priority) under a
+        int old = atomicCAS(parent + b, b, a);
+        if (old == b)
+            return;
+        b = old;
+    }
+}
+
+// ---- Morton interleave (21 bits per axis -> 63 bits) ------------------------
+__device__ __forceinline__ unsigned long long spread3(unsigned v)
+{
+    unsigned long long x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+}  // namespace abx

@@ -1,0 +1,274 @@
+// Fused traversals: core counting, pair traversal with union-find, border
+// points and the final labels.
+//
+// Paper, Algorithm PDSDbscan: if minPts > 2 the core points are found first
+// (a counting traversal per point, stopped once the count reaches minPts --
+// subsection "Early termination"); then every pair of neighbours is visited
+// once and core-core pairs are merged with Union.  Subsection "FDBSCAN": the
+// traversal is fused with counting and with union-find (no neighbour lists,
+// O(n) memory), and the merging kernel uses pair traversal (subsection "Pair
+// traversal"): the thread of point i starts at its own leaf and follows ropes,
+// so it only meets leaves after its own and each pair is seen exactly once.
+//
+// The paper's border step (the first core to arrive claims an unclaimed
+// non-core neighbour inside a critical section) is nondeterministic.  It is
+// replaced by a separate pass after all unions: each non-core point looks at
+// all its core neighbours and joins the cluster whose smallest core index is
+// smallest.
+#include "work.cuh"
+
+namespace abx {
+
+struct Tree {
+    const float4 *__restrict__ nodes;
+    const int *__restrict__ leaf_first;
+    int L;
+};
+
+// A traversal visits every node at most once; a node index outside the
+// hierarchy or more steps than nodes means a corrupted tree: the traversal
+// stops and records DEV_INTERNAL instead of faulting or spinning.
+__device__ __forceinline__ bool node_ok(int node, int L, unsigned &steps, unsigned *dev_status)
+{
+    if ((unsigned)node >= (unsigned)(2 * L - 1) || ++steps > (unsigned)(2 * L)) {
+        atomicOr(dev_status, DEV_INTERNAL);
+        return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ float4 node_lo(const Tree &t, int i) { return __ldg(t.nodes + 2 * (size_t)i); }
+__device__ __forceinline__ float4 node_hi(const Tree &t, int i) { return __ldg(t.nodes + 2 * (size_t)i + 1); }
+
+// ---- pair traversal with union-find ------------------------------------------------
+// FoF (minPts <= 2): every neighbour pair is merged and both ends become core.
+// DBSCAN (minPts > 2): only core threads run, and only core-core pairs merge.
+
+template <bool FOF>
+__global__ void k_union(int64_t n, const State *__restrict__ st,
+                                               const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                                               const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
+                                               int *parent, unsigned char *core, float e2, unsigned *dev_status)
+{
+    const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i64 >= n)
+        return;
+    const int i = (int)i64;
+    if (!FOF && !core[i])
+        return;
+    const Tree T{nodes, leaf_first, st->n_leaves};
+    const int L = T.L;
+    const float4 p = spts[i];
+    bool found = false;
+
+    const int my_leaf = L - 1 + leaf_of[i];
+    const unsigned w0 = __float_as_uint(node_lo(T, my_leaf).w);
+    if (!(w0 & DENSE_BIT)) {
+        const int e = leaf_first[my_leaf - (L - 1) + 1];
+        for (int j = i + 1; j < e; j++) {
+            float4 q = __ldg(spts + j);
+            if ((FOF || core[j]) && dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
+                uf_unite(parent, spts, i, j);
+                if (FOF) {
+                    found = true;
+                    core[j] = 1;
+                }
+            }
+        }
+    }
+    int node = __float_as_int(node_hi(T, my_leaf).w);
+    unsigned steps = 0;
+    while (node != SENTINEL) {
+        if (!node_ok(node, L, steps, dev_status))
+            break;
+        const float4 lo = node_lo(T, node), hi = node_hi(T, node);
+        if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2) {
+            if (node < L - 1) {
+                node = __float_as_int(lo.w);
+                continue;
+            }
+            const unsigned lw = __float_as_uint(lo.w);
+            const int s = (int)(lw & ~DENSE_BIT);
+            const int e = leaf_first[node - (L - 1) + 1];
+            if (lw & DENSE_BIT) {
+                // all points of a dense cell are core and already one set:
+                // one link is enough, none if i is already in that set
+                if (uf_find(parent, i) == uf_find(parent, s)) {
+                    found = true;
+                } else {
+                    for (int j = s; j < e; j++) {
+                        float4 q = __ldg(spts + j);
+                        if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
+                            uf_unite(parent, spts, i, s);
+                            found = true;
+                            break;
+                        }
+                    }
+                }
+            } else {
+                for (int j = s; j < e; j++) {
+                    float4 q = __ldg(spts + j);
+                    if ((FOF || core[j]) && dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
+                        uf_unite(parent, spts, i, j);
+                        if (FOF) {
+                            found = true;
+                            core[j] = 1;
+                        }
+                    }
+                }
+            }
+        }
+        node = __float_as_int(hi.w);
+    }
+    if (FOF && found)
+        core[i] = 1;
+}
+
+// ---- core counting with early termination (minPts > 2) -------------------------------
+
+__global__ void k_count(int64_t n, const State *__restrict__ st,
+                                               const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                                               const int *__restrict__ leaf_first, unsigned char *core, float e2,
+                                               int minpts, unsigned *dev_status)
+{
+    const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i64 >= n)
+        return;
+    const int i = (int)i64;
+    if (core[i])
+        return;  // member of a dense cell
+    const Tree T{nodes, leaf_first, st->n_leaves};
+    const int L = T.L;
+    const float4 p = spts[i];
+    int cnt = 0;
+    int node = st->root;
+    unsigned steps = 0;
+    while (node != SENTINEL) {
+        if (!node_ok(node, L, steps, dev_status))
+            break;
+        const float4 lo = node_lo(T, node), hi = node_hi(T, node);
+        if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2) {
+            if (node < L - 1) {
+                node = __float_as_int(lo.w);
+                continue;
+            }
+            const int s = (int)(__float_as_uint(lo.w) & ~DENSE_BIT);
+            const int e = leaf_first[node - (L - 1) + 1];
+            for (int j = s; j < e; j++) {
+                float4 q = __ldg(spts + j);
+                if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2 && ++cnt >= minpts) {
+                    core[i] = 1;
+                    return;
+                }
+            }
+        }
+        node = __float_as_int(hi.w);
+    }
+}
+
+// ---- border points (minPts > 2) ----------------------------------------------------------
+// For a non-core point b: the root with the smallest priority (= K(C)) among
+// the clusters of its core neighbours.  The choice is recorded as parent[b]
+// (b is never in a union, so nothing else reads or writes that word) and the
+// cluster's smallest border index is kept in bmin[root].
+
+__global__ void k_border(int64_t n, const State *__restrict__ st,
+                                                const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                                                const int *__restrict__ leaf_first, int *parent,
+                                                const unsigned char *__restrict__ core, int *bmin, float e2,
+                                                unsigned *dev_status)
+{
+    const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i64 >= n)
+        return;
+    const int i = (int)i64;
+    if (core[i])
+        return;
+    const Tree T{nodes, leaf_first, st->n_leaves};
+    const int L = T.L;
+    const float4 p = spts[i];
+    int best_k = 0x7fffffff, best_r = -1;
+    int node = st->root;
+    unsigned steps = 0;
+    while (node != SENTINEL) {
+        if (!node_ok(node, L, steps, dev_status))
+            break;
+        const float4 lo = node_lo(T, node), hi = node_hi(T, node);
+        if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2) {
+            if (node < L - 1) {
+                node = __float_as_int(lo.w);
+                continue;
+            }
+            const unsigned lw = __float_as_uint(lo.w);
+            const int s = (int)(lw & ~DENSE_BIT);
+            const int e = leaf_first[node - (L - 1) + 1];
+            for (int j = s; j < e; j++) {
+                if (!core[j])
+                    continue;
+                float4 q = __ldg(spts + j);
+                if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
+                    int r = uf_find(parent, j);
+                    int k = orig_of(spts, r);
+                    if (k < best_k) {
+                        best_k = k;
+                        best_r = r;
+                    }
+                    if (lw & DENSE_BIT)
+                        break;  // one cluster per dense cell
+                }
+            }
+        }
+        node = __float_as_int(hi.w);
+    }
+    if (best_r >= 0) {
+        parent[i] = best_r;
+        atomicMin(bmin + best_r, __float_as_int(p.w));
+    }
+}
+
+// ---- labels -----------------------------------------------------------------------------------
+// Cluster id = the smallest original index among the members: the root's
+// (smallest core index) or a smaller border index.  Scattered to input order.
+
+template <bool FOF>
+__global__ void __launch_bounds__(256) k_finalize(int64_t n, const float4 *__restrict__ spts, int *parent,
+                                                  const unsigned char *__restrict__ core,
+                                                  const int *__restrict__ bmin, int32_t *labels)
+{
+    const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i64 >= n)
+        return;
+    const int i = (int)i64;
+    int lab = -1;
+    if (core[i]) {
+        int r = uf_find(parent, i);
+        lab = orig_of(spts, r);
+        if (!FOF)
+            lab = min(lab, bmin[r]);
+    } else if (!FOF) {
+        int r = parent[i];
+        if (r != i)
+            lab = min(orig_of(spts, r), bmin[r]);
+    }
+    const int o = __float_as_int(spts[i].w);
+    if ((unsigned)o < (unsigned)n)
+        labels[o] = lab;
+}
+
+void stage_cluster(const Work &w, float eps, int minpts, const Params &p, int32_t *labels, cudaStream_t s)
+{
+    const float e2 = eps * eps;
+    const int B = p.block;
+    const int g = div_up(w.n, B);
+    if (minpts <= 2) {
+        k_union<true><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent, w.core, e2, w.dev_status);
+        k_finalize<true><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.spts, w.parent, w.core, w.bmin, labels);
+    } else {
+        k_count<<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_first, w.core, e2, minpts, w.dev_status);
+        k_union<false><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent, w.core, e2, w.dev_status);
+        k_border<<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_first, w.parent, w.core, w.bmin, e2, w.dev_status);
+        k_finalize<false><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.spts, w.parent, w.core, w.bmin, labels);
+    }
+}
+
+}  // namespace abx

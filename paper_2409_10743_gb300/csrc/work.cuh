@@ -1,0 +1,60 @@
+// Workspace layout of one clustering call and the launchers of each stage.
+#pragma once
+
+#include "abx_internal.cuh"
+
+namespace abx {
+
+// Resolved tuning parameters.
+struct Params {
+    int leaf_size;   // points per ordinary leaf (1..32)
+    int dense;       // dense-cell leaves on/off
+    int sub_bits;    // Morton bits per axis below the dense-cell side
+    int block;       // threads per block of the traversal kernels
+};
+
+// Device buffers of one call; sizes are for n points (L <= n leaves).
+struct Work {
+    int64_t n;
+    int n_sms;
+    unsigned *dev_status;            // per-device status word
+    State *st;
+    unsigned long long *keys[2];     // Morton keys, radix double buffer
+    unsigned *vals[2];               // original indices, radix double buffer
+    unsigned long long *sort_lb;     // [MAX_PASSES][tiles][RADIX] look-back words
+    unsigned long long *scan_lb;     // [2][scan tiles] look-back words
+    float4 *spts;                    // sorted points: x, y, z, original index (as int bits)
+    int *cell_id;                    // [n] cell of each sorted point
+    int *cell_start;                 // [n + 1]
+    unsigned char *cell_dense;       // [n]
+    int *cell_root;                  // [n] member with the smallest original index
+    int *leaf_of;                    // [n] leaf of each sorted point
+    int *leaf_first;                 // [n + 1] first sorted point of each leaf
+    unsigned char *delta;            // [n] split level between leaves t and t+1
+    float4 *nodes;                   // [2 * (2n - 1)] hierarchy records (lo, hi)
+    unsigned long long *slot;        // [n] bottom-up meeting slots
+    int *right_of;                   // [n] right child of each internal node
+    int *parent;                     // [n] union-find parents (sorted positions)
+    unsigned char *core;             // [n] core flags
+    int *bmin;                       // [n] smallest border index per cluster root
+    size_t sort_tiles, scan_tiles;
+};
+
+size_t work_bytes(int64_t n);
+void work_carve(Work &w, void *base, int64_t n);
+
+// Stages (all asynchronous on `s`).
+void stage_bounds_quant(const Work &w, const float *points, float eps, const Params &p, cudaStream_t s);
+void stage_morton_sort(const Work &w, const float *points, cudaStream_t s);
+void stage_gather(const Work &w, const float *points, int minpts, cudaStream_t s);
+void stage_cells_leaves(const Work &w, float eps, int minpts, const Params &p, cudaStream_t s);
+void stage_hierarchy(const Work &w, cudaStream_t s);
+void stage_cluster(const Work &w, float eps, int minpts, const Params &p, int32_t *labels,
+                   cudaStream_t s);
+
+// One-time per-device kernel attributes.
+void kernels_init_device();
+
+__host__ __device__ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace abx

@@ -1,0 +1,212 @@
+"""GPU parity: labels from the CUDA library (through the C ABI) must equal the
+oracle's bit for bit -- labels are integers, so the bar is exact equality --
+on the hand cases, small seeded cases over many tuning parameters, and the
+full-size configurations.  Also edge cases, determinism, and the device
+status word."""
+import numpy as np
+import pytest
+
+import oracle
+from cases import _cases, _clumpy
+from conftest import golden_cases
+from workloads import CONFIGS, clumps, scaled
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def abx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_10743_gb300 import binding
+    binding.lib()
+    assert binding.device_status() == 0
+    return binding
+
+
+def gpu_labels(abx, p, eps, minpts, params=None):
+    t = torch.from_numpy(np.ascontiguousarray(p, np.float32)).cuda()
+    lab = abx.dbscan(t, eps, minpts, params=params)
+    torch.cuda.synchronize()
+    assert abx.device_status() == 0
+    return lab.cpu().numpy()
+
+
+def assert_same(got, want, what=""):
+    if not np.array_equal(got, want):
+        bad = np.nonzero(got != want)[0]
+        raise AssertionError(f"{what}: {bad.size} of {got.size} labels differ; first at {bad[:8]}: "
+                             f"got {got[bad[:8]]}, want {want[bad[:8]]}")
+
+
+@pytest.mark.parametrize("case", golden_cases(), ids=lambda c: c[0])
+def test_golden(abx, case):
+    name, p, eps, minpts, want = case
+    assert_same(gpu_labels(abx, p, eps, minpts), want, name)
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
+def test_small_cases(abx, case):
+    name, p, eps, minpts = case
+    assert_same(gpu_labels(abx, p, eps, minpts), oracle.dbscan(p, eps, minpts), name)
+
+
+PARAMS = [dict(leaf_size=1), dict(leaf_size=2), dict(leaf_size=8), dict(leaf_size=32),
+          dict(dense_cells=-1), dict(sub_bits=0), dict(sub_bits=8), dict(block=128),
+          dict(block=1024), dict(leaf_size=1, dense_cells=-1)]
+
+
+@pytest.mark.parametrize("kw", PARAMS, ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
+def test_parameters_never_change_labels(abx, kw):
+    rng = np.random.default_rng(77)
+    for minpts, eps, p in [(2, 0.02, _clumpy(rng, 6000, 12, 0.01)), (5, 0.03, _clumpy(rng, 6000, 12, 0.01)),
+                           (2, 0.0, np.repeat(_clumpy(rng, 500, 5, 0.01), 3, axis=0))]:
+        assert_same(gpu_labels(abx, p, eps, minpts, abx.Params(**kw)), oracle.dbscan(p, eps, minpts), str(kw))
+
+
+def test_empty_and_single(abx):
+    t = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    assert abx.dbscan(t, 0.1, 2).numel() == 0
+    one = np.array([[0.5, 0.5, 0.5]], np.float32)
+    assert gpu_labels(abx, one, 0.1, 1).tolist() == [0]
+    assert gpu_labels(abx, one, 0.1, 2).tolist() == [-1]
+
+
+def test_all_identical_points(abx):
+    p = np.full((5000, 3), 0.25, np.float32)
+    assert (gpu_labels(abx, p, 0.0, 2) == 0).all()
+    assert (gpu_labels(abx, p, 0.0, 5001) == -1).all()
+    assert (gpu_labels(abx, p, 0.1, 7) == 0).all()
+
+
+def test_ragged_tiles(abx):
+    """Sizes around the sort and scan tile (4096) and the block size."""
+    rng = np.random.default_rng(3)
+    for n in [255, 256, 257, 4095, 4096, 4097, 8193, 12289]:
+        p = _clumpy(rng, n, 6, 0.01)
+        for minpts in (2, 4):
+            assert_same(gpu_labels(abx, p, 0.02, minpts), oracle.dbscan(p, 0.02, minpts), f"n={n}")
+
+
+def test_unaligned_points(abx):
+    """A points pointer that is not 16-byte aligned takes the scalar bounds path."""
+    rng = np.random.default_rng(8)
+    p = _clumpy(rng, 3001, 6, 0.01)
+    flat = torch.from_numpy(np.concatenate([[0.0], p.ravel()]).astype(np.float32)).cuda()
+    view = flat[1:].view(-1, 3)
+    assert view.data_ptr() % 16 != 0
+    lab = abx.dbscan(view, 0.02, 3)
+    torch.cuda.synchronize()
+    assert_same(lab.cpu().numpy(), oracle.dbscan(p, 0.02, 3), "unaligned")
+
+
+def test_extreme_coordinates(abx):
+    rng = np.random.default_rng(12)
+    p = (_clumpy(rng, 4000, 6, 0.01) * 1e6 - 3e5).astype(np.float32)
+    assert_same(gpu_labels(abx, p, 2e4, 3), oracle.dbscan(p, 2e4, 3), "scaled")
+    p = (_clumpy(rng, 4000, 6, 0.01) * 1e-20).astype(np.float32)
+    assert_same(gpu_labels(abx, p, 2e-22, 2), oracle.dbscan(p, 2e-22, 2), "tiny")
+    # eps far larger than the extent: one cluster
+    q = _clumpy(rng, 3000, 6, 0.01)
+    assert_same(gpu_labels(abx, q, 10.0, 5), oracle.dbscan(q, 10.0, 5), "huge eps")
+
+
+def test_deterministic(abx):
+    p = clumps(200_000, 200, 31, a0=0.02)
+    eps = 0.004
+    a = gpu_labels(abx, p, eps, 2)
+    for _ in range(3):
+        assert np.array_equal(gpu_labels(abx, p, eps, 2), a)
+
+
+def test_nonfinite_sets_status(abx):
+    p = _clumpy(np.random.default_rng(2), 1000, 4, 0.01)
+    p[17, 1] = np.nan
+    t = torch.from_numpy(p).cuda()
+    abx.dbscan(t, 0.02, 2)
+    assert abx.device_status() == abx.ABX_ENONFINITE
+    assert abx.device_status() == 0  # cleared
+
+
+def test_host_entry_point(abx):
+    p = clumps(100_000, 100, 41, a0=0.02)
+    eps = 0.005
+    assert_same(abx.dbscan_host(p, eps, 3), oracle.dbscan(p, eps, 3), "host")
+
+
+def test_batch_equals_single(abx):
+    rng = np.random.default_rng(5)
+    sizes = [0, 1, 700, 5000, 33, 20000]
+    segs = [_clumpy(rng, n, 5, 0.01) if n else np.zeros((0, 3), np.float32) for n in sizes]
+    eps = [0.02, 0.1, 0.03, 0.02, 0.5, 0.01]
+    mp = [2, 1, 5, 2, 3, 10]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    allp = torch.from_numpy(np.concatenate(segs).astype(np.float32)).cuda()
+    lab = abx.dbscan_batch(allp, off, eps, mp)
+    torch.cuda.synchronize()
+    assert abx.device_status() == 0
+    lab = lab.cpu().numpy()
+    for k in range(len(sizes)):
+        assert_same(lab[off[k]:off[k + 1]], oracle.dbscan(segs[k], eps[k], mp[k]), f"segment {k}")
+
+
+def test_bvh_count_early_termination(abx):
+    rng = np.random.default_rng(9)
+    p = _clumpy(rng, 20000, 10, 0.02)
+    q = _clumpy(rng, 3000, 10, 0.02)
+    eps = 0.02
+    import brute
+    full = np.array([brute.adjacency_rows(np.concatenate([q[i:i + 1], p]), eps, slice(0, 1))[0, 1:].sum()
+                     for i in range(200)])
+    h = abx.BVH(torch.from_numpy(p).cuda(), leaf_size=4)
+    info = h.info()
+    assert info["n_points"] == len(p) and 1 <= info["n_leaves"] <= len(p) and info["levels"] >= 2
+    for cap in (1, 5, 1000000):
+        got = h.count(torch.from_numpy(q[:200]).cuda(), eps, cap).cpu().numpy()
+        assert np.array_equal(got, np.minimum(full, cap))
+    h.close()
+
+
+# ---- full-size configurations ------------------------------------------------------
+
+def _full(abx, name):
+    cfg = CONFIGS[name]
+    p = cfg.points()
+    got = gpu_labels(abx, p, cfg.eps, cfg.minpts)
+    want = oracle.dbscan(p, cfg.eps, cfg.minpts)
+    assert_same(got, want, cfg.describe())
+    return got
+
+
+def test_c1_full(abx):
+    _full(abx, "C1")
+
+
+@pytest.mark.slow
+def test_c2_full(abx):
+    _full(abx, "C2")
+
+
+@pytest.mark.slow
+def test_c2_stress_full(abx):
+    _full(abx, "C2h")
+
+
+@pytest.mark.slow
+def test_c3_full(abx):
+    _full(abx, "C3")
+
+
+@pytest.mark.slow
+def test_c4_full(abx):
+    """2^27 points, FoF: the benchmark's workload, compared label by label."""
+    _full(abx, "C4")
+
+
+@pytest.mark.parametrize("name", ["C2", "C3", "C2h"])
+def test_scaled_configs(abx, name):
+    cfg = scaled(CONFIGS[name], 300_000)
+    p = cfg.points()
+    assert_same(gpu_labels(abx, p, cfg.eps, cfg.minpts), oracle.dbscan(p, cfg.eps, cfg.minpts), cfg.describe())

@@ -123,7 +123,7 @@ def blobs(n: int, n_blobs: int, seed: int, blob_frac: float = 0.8,
     for s in range(0, n_in, chunk):
         o = owner[s:s + chunk]
         z = rng.standard_normal((o.size, 3)) * sig[o]
-        out[s:s + chunk] = (centres[o] + np.einsum("nij,nj->ni", q[o], z)).astype(np.float32)
+        out[s:s + o.size] = (centres[o] + np.einsum("nij,nj->ni", q[o], z)).astype(np.float32)
     out[n_in:] = rng.random((n - n_in, 3), dtype=np.float32)
     return out[rng.permutation(n)]
 
