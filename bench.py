@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark: friends-of-friends clustering throughput on one GB300.
+
+Workload (one "step" = one full clustering pass: bounds, Morton codes, radix
+sort, gather, dense cells, leaves, hierarchy build, pair traversal with
+union-find, labels): 2^27 = 134,217,728 FP32 points in the unit box, 60% in
+50,000 Plummer clumps (power-law masses, slope -1.9) and 40% uniform,
+minPts = 2, eps = 0.168 * N^(-1/3) = 3.28125e-4 -- the per-rank-scale
+halo-finding configuration.  Points are synthetic (seeded) and resident in
+HBM when the timed region starts; they (1.6 GB) and the working set (~20 GB)
+are far larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+Prints one JSON line: value (Mpoints/s, whole job), ms_per_step, the
+end-to-end number through the host-memory entry point (copies inside the timed
+region), the roofline of the dominant kernel, the oracle's CPU baseline,
+clocks sampled during the timed region and the number of kernels launched.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank clusters its own independent instance
+(weak scaling: replicas, no collective on the data path); the timed region is
+bracketed by barriers and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FoF/DBSCAN Mpoints/s at 134M pts (frac. HBM peak); batched p50/p99 vs plain"
+UNIT = "Mpoints/s"
+
+
+# ---- algorithmic (compulsory) bytes per point of each stage ----------------------
+# Each input read once, each output written once; what the method avoids (the
+# neighbour lists, the pair tests inside dense cells) is not counted.
+def stage_bytes(stage: str, c: dict, n: int) -> float:
+    P = max(1, c.get("radix_passes", 6))
+    L = max(1, c.get("leaves", n // 4))
+    per_leaf = L / n
+    table = {
+        "bounds": 12.0,                                   # read xyz
+        "morton": 12.0 + 8.0,                             # read xyz, write key
+        "sort": 20.0 + (P - 1) * 24.0,                    # 1st pass: key in, key+idx out; then 24/pass
+        "gather": 4.0 + 12.0 + 16.0 + 4.0 + 1.0,          # perm, xyz, sorted float4, parent, core
+        "cells": 8.0 + 4.0 + 1.0,                         # keys, cell id, cell flags
+        "leaves": 4.0 + 4.0 + 16.0 + per_leaf * (32.0 + 16.0 + 1.0),  # cell id, leaf id, points; leaf records
+        "build": per_leaf * (32.0 + 1.0 + 32.0 + 8.0 + 4.0 + 8.0),      # leaf box, delta, node, slot, child, rope
+        "count": 16.0 + 1.0,
+        "union": 16.0 + 4.0 + 4.0 + 1.0 + per_leaf * 2 * 32.0,        # point, leaf id, parent, core; nodes once
+        "border": 16.0 + 1.0,
+        "finalize": 16.0 + 1.0 + 4.0 + 4.0,               # point, core, parent, label
+    }
+    return table.get(stage, 0.0)
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def hbm_peak() -> tuple[float, str]:
+    pk = measured_peaks()
+    if pk.get("hbm_gbs"):
+        return float(pk["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(stage: str):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu
+    summary, when it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        from paper_2409_10743_gb300 import build as b
+        if d.get("csrc_sha") != b.source_hash():
+            return None
+        return d.get("stages", {}).get(stage, {}).get("dram_bytes_per_point_launch")
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling in the background during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(cfg, p: np.ndarray, frac_x: float) -> dict:
+    """The oracle, as it stands, single-threaded on a bounded sample of the same
+    workload: the points with x < frac_x (same density, eps and mixture)."""
+    import oracle
+    sel = p[p[:, 0] < frac_x]
+    t0 = time.perf_counter()
+    oracle.dbscan(sel, cfg.eps, cfg.minpts)
+    dt = time.perf_counter() - t0
+    return {"value": round(len(sel) / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(sel)} points with x < {frac_x} of the same workload ({dt:.1f} s, 1 thread)"}
+
+
+def rank_config(base, rank: int, ws: int):
+    """Replicas: rank r clusters its own instance of the workload (seed offset
+    by 100 r); with one rank the workload is the configuration itself."""
+    from workloads import Config
+    if ws == 1:
+        return base
+    return Config(base.name, base.n, base.eps, base.minpts, base.kind, base.seed + 100 * rank, base.n_groups,
+                  base.a_scale)
+
+
+def reduce_max(x: float, ws: int, device=None) -> float:
+    """The slowest rank's time (max over ranks); identity for one rank."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, ws, rank):
+    """The oracle arm: the CPU oracle on the host cores, each step a bounded
+    sample of the workload (rank 0 only)."""
+    if rank != 0:
+        return
+    from workloads import CONFIGS
+    cfg = CONFIGS[args.config]
+    p = cfg.points()
+    frac = args.ref_frac
+    sel = np.ascontiguousarray(p[p[:, 0] < frac])
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.dbscan(sel, cfg.eps, cfg.minpts)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.dbscan(sel, cfg.eps, cfg.minpts)
+    dt = time.perf_counter() - t0
+    value = len(sel) * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg.describe(), "sample": f"points with x < {frac} ({len(sel)} points)"},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(sel)} points with x < {frac} of {cfg.name}, per step"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="abx", choices=["abx", "reference"])
+    ap.add_argument("--config", default="C4")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-frac", type=float, default=0.125)
+    ap.add_argument("--ref-frac", type=float, default=0.0625)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    ws, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    from workloads import CONFIGS
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2409_10743_gb300 import binding as abx
+    abx.lib()
+
+    cfg = rank_config(CONFIGS[args.config], rank, ws)
+    p = cfg.points()
+    n = cfg.n
+    t = torch.from_numpy(p).cuda()
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        abx.dbscan(t, cfg.eps, cfg.minpts, labels=labels)
+    torch.cuda.synchronize()
+    st = abx.device_status()
+    if st != 0:
+        raise SystemExit(f"device status after warm-up: {abx.status_str(st)}")
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- timed region: K steps, stage events on the launching stream ----
+    abx.profile_enable(True)
+    clocks = Clocks(local)
+    stage_ms = []
+    launches0 = abx.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        abx.dbscan(t, cfg.eps, cfg.minpts, labels=labels)
+        stage_ms.append(abx.profile_read())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = abx.launch_count() - launches0
+    counters = abx.profile_counters()
+    abx.profile_enable(False)
+    ms = e0.elapsed_time(e1)
+    st = abx.device_status()
+    if st != 0:
+        raise SystemExit(f"device status after timed region: {abx.status_str(st)}")
+    ms = reduce_max(ms, ws, "cuda")
+    ms_step = ms / args.steps
+    value = n * ws * args.steps / (ms / 1e3) / 1e6
+
+    # ---- end to end through the host-memory entry point ----
+    host_pts = torch.from_numpy(p).pin_memory()
+    host_lab = torch.empty(n, dtype=torch.int32).pin_memory()
+    lib = abx.lib()
+    s_ptr = abx._stream(None)
+    rc = lib.abx_dbscan_host(host_pts.data_ptr(), n, float(np.float32(cfg.eps)), cfg.minpts,
+                             host_lab.data_ptr(), s_ptr)
+    assert rc == 0, abx.status_str(rc)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        rc = lib.abx_dbscan_host(host_pts.data_ptr(), n, float(np.float32(cfg.eps)), cfg.minpts,
+                                 host_lab.data_ptr(), s_ptr)
+        assert rc == 0, abx.status_str(rc)
+    dt = time.perf_counter() - t0
+    barrier()
+    dt = reduce_max(dt, ws, "cuda")
+    e2e = {"value": round(n * ws * args.e2e_steps / dt / 1e6, 3), "unit": UNIT,
+           "h2d_bytes_per_step": int(host_pts.numel() * 4), "d2h_bytes_per_step": int(host_lab.numel() * 4),
+           "api": "abx_dbscan_host (pinned host buffers, copies inside the timed region)"}
+    assert np.array_equal(host_lab.numpy(), labels.cpu().numpy()), "host and device paths disagree"
+
+    # ---- roofline of the dominant stage ----
+    names = list(stage_ms[0].keys())
+    mean_ms = {k: float(np.mean([s[k] for s in stage_ms])) for k in names}
+    dom = max(mean_ms, key=mean_ms.get)
+    peak, peak_kind = hbm_peak()
+    alg = stage_bytes(dom, counters, n) * n
+    achieved = alg / (mean_ms[dom] / 1e3) / 1e9
+    traffic_pp = ncu_traffic(dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None if traffic_pp is None else int(traffic_pp * n),
+            "algorithmic_bytes": int(alg), "peak_source": peak_kind}
+    total_alg = sum(stage_bytes(k, counters, n) for k in names) * n
+    pipeline = {"algorithmic_bytes_per_point": round(total_alg / n, 1),
+                "achieved_gbs": round(total_alg / (ms_step / 1e3) / 1e9, 1),
+                "frac_of_peak": round(total_alg / (ms_step / 1e3) / 1e9 / peak, 4)}
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg.describe(), "n_points": n, "eps": cfg.eps, "minpts": cfg.minpts,
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single instance",
+                       "l2": "no flush: inputs (1.6 GB) and working set exceed the 129 MB L2"},
+            "e2e": e2e, "roofline": roof, "pipeline": pipeline,
+            "stage_ms": {k: round(v, 3) for k, v in mean_ms.items()}, "counters": counters,
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, p, args.cpu_frac)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,37 @@ abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t
                             const float *eps, const int32_t *minpts, int32_t *labels,
                             abx_stream stream);
 
+/* ---- stage timers (tracing) -------------------------------------------------- */
+
+/*
+ * abx_profile_enable -- when on, every clustering call records a CUDA event on
+ * its stream at each stage boundary (bounds, morton, sort, gather, cells,
+ * leaves, build, count, union, border, finalize).  Meant for one call at a
+ * time (benchmarks): concurrent profiled calls overwrite each other's events.
+ */
+abx_status abx_profile_enable(int32_t on);
+
+/* Number of stages and the name of stage i (static storage). */
+int32_t abx_profile_stage_count(void);
+const char *abx_profile_stage_name(int32_t i);
+
+/*
+ * abx_profile_read -- wait for the stream of the most recent profiled call and
+ * write the milliseconds each stage took (device time between consecutive
+ * stage events) into ms[0 .. n-1].  Stages a call skipped read 0.
+ */
+abx_status abx_profile_read(float *ms, int32_t n);
+
+/*
+ * abx_profile_counters -- facts about the most recent profiled clustering
+ * call, written to out[0 .. n-1] in this order: radix passes run, Morton bits
+ * per axis, dense cells on (0/1), cells, hierarchy leaves, root node.
+ */
+abx_status abx_profile_counters(int64_t *out, int32_t n);
+
+/* Total number of kernels this library has launched in this process. */
+unsigned long long abx_launch_count(void);
+
 /* ---- the bounding volume hierarchy on its own ------------------------------ */
 
 /* Opaque, library-owned hierarchy over a point set (paper, section "ArborX

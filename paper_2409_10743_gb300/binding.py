@@ -49,6 +49,12 @@ _SIGS = {
     "abx_bvh_count": (_i32, [_vp, _vp, _i64, _f32, _i32, _vp, _vp]),
     "abx_bvh_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32), _vp]),
     "abx_bvh_destroy": (_i32, [_vp]),
+    "abx_profile_enable": (_i32, [_i32]),
+    "abx_profile_stage_count": (_i32, []),
+    "abx_profile_stage_name": (ctypes.c_char_p, [_i32]),
+    "abx_profile_read": (_i32, [_vp, _i32]),
+    "abx_launch_count": (ctypes.c_uint64, []),
+    "abx_profile_counters": (_i32, [_vp, _i32]),
 }
 
 
@@ -147,6 +153,33 @@ def dbscan_batch(points, offsets, eps, minpts, labels=None, stream=None):
 def device_status(stream=None) -> int:
     """Wait for the stream; return and clear the device status word."""
     return int(lib().abx_device_status(_stream(stream)))
+
+
+def profile_enable(on: bool = True) -> None:
+    """Record CUDA events at every stage boundary of each clustering call."""
+    _check(lib().abx_profile_enable(1 if on else 0), "abx_profile_enable")
+
+
+def profile_read() -> dict:
+    """Milliseconds per stage of the most recent profiled call."""
+    L = lib()
+    n = L.abx_profile_stage_count()
+    ms = np.zeros(n, dtype=np.float32)
+    _check(L.abx_profile_read(ms.ctypes.data, n), "abx_profile_read")
+    return {L.abx_profile_stage_name(i).decode(): float(ms[i]) for i in range(n)}
+
+
+def profile_counters() -> dict:
+    """Radix passes, Morton bits per axis, dense on, cells, leaves, root of the
+    most recent profiled call."""
+    v = np.zeros(6, dtype=np.int64)
+    _check(lib().abx_profile_counters(v.ctypes.data, 6), "abx_profile_counters")
+    return dict(zip(["radix_passes", "morton_bits", "dense_cells", "cells", "leaves", "root"], map(int, v)))
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().abx_launch_count())
 
 
 class BVH:

@@ -38,6 +38,17 @@ def _deps():
         os.path.join(HERE, "..", "include", "abx.h")]
 
 
+def source_hash() -> str:
+    """sha256 over the kernel sources and the public header (identifies the
+    kernels a profile was taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for d in _deps():
+        with open(d, "rb") as f:
+            h.update(os.path.basename(d).encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False

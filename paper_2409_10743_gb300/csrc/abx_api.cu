@@ -1,4 +1,5 @@
 // The C ABI: argument checks, per-device context, workspace, stage sequence.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -63,6 +64,47 @@ abx_status bvh_device_ctx(cudaMemPool_t *pool, unsigned **status, int *n_sms)
         *n_sms = c->n_sms;
     }
     return rc;
+}
+
+// ---- stage timers and launch accounting ------------------------------------------
+
+static std::atomic<unsigned long long> g_launches{0};
+static std::atomic<int> g_prof_on{0};
+static std::mutex g_prof_mu;
+static cudaEvent_t g_ev[ST_NUM + 1];
+static bool g_ev_ready = false;
+static bool g_ev_marked[ST_NUM + 1];
+static cudaStream_t g_prof_stream = nullptr;
+static State *g_prof_state = nullptr;  // pinned host copy of the last profiled call's state
+
+void note_launch(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+
+void prof_begin(cudaStream_t s)
+{
+    if (!g_prof_on.load())
+        return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_ev_ready) {
+        for (int i = 0; i <= ST_NUM; i++)
+            cudaEventCreate(&g_ev[i]);
+        g_ev_ready = true;
+    }
+    for (int i = 0; i <= ST_NUM; i++)
+        g_ev_marked[i] = false;
+    cudaEventRecord(g_ev[0], s);
+    g_ev_marked[0] = true;
+    g_prof_stream = s;
+}
+
+void prof_mark(int stage, cudaStream_t s)
+{
+    if (!g_prof_on.load())
+        return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_ev_ready || stage < 0 || stage >= ST_NUM)
+        return;
+    cudaEventRecord(g_ev[stage + 1], s);
+    g_ev_marked[stage + 1] = true;
 }
 
 // ---- workspace ------------------------------------------------------------------------
@@ -167,12 +209,22 @@ static abx_status cuda_status(cudaError_t e)
 static void run_pipeline(Work &w, const float *points, float eps, int minpts, int32_t *labels, const Params &p,
                          cudaStream_t s)
 {
+    prof_begin(s);
     stage_bounds_quant(w, points, eps, p, s);
     stage_morton_sort(w, points, s);
     stage_gather(w, points, minpts, s);
     stage_cells_leaves(w, eps, minpts, p, s);
     stage_hierarchy(w, s);
     stage_cluster(w, eps, minpts, p, labels, s);
+    if (g_prof_on.load()) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_prof_state && cudaMallocHost((void **)&g_prof_state, sizeof(State)) != cudaSuccess) {
+            g_prof_state = nullptr;
+            cudaGetLastError();
+        }
+        if (g_prof_state)
+            cudaMemcpyAsync(g_prof_state, w.st, sizeof(State), cudaMemcpyDeviceToHost, s);
+    }
 }
 
 }  // namespace abx
@@ -294,6 +346,60 @@ abx_status abx_device_status(abx_stream stream)
         return ABX_ETIMEOUT;
     if (v & DEV_NONFINITE)
         return ABX_ENONFINITE;
+    return ABX_OK;
+}
+
+static const char *k_stage_names[ST_NUM] = {"bounds", "morton", "sort", "gather", "cells", "leaves",
+                                           "build", "count", "union", "border", "finalize"};
+
+abx_status abx_profile_enable(int32_t on)
+{
+    g_prof_on.store(on ? 1 : 0);
+    return ABX_OK;
+}
+
+int32_t abx_profile_stage_count(void) { return ST_NUM; }
+
+const char *abx_profile_stage_name(int32_t i) { return (i >= 0 && i < ST_NUM) ? k_stage_names[i] : ""; }
+
+abx_status abx_profile_read(float *ms, int32_t n)
+{
+    if (!ms || n < 1)
+        return ABX_EINVAL;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_ev_ready || !g_ev_marked[0])
+        return ABX_EINVAL;
+    if (cudaStreamSynchronize(g_prof_stream) != cudaSuccess)
+        return ABX_ECUDA;
+    int prev = 0;
+    for (int i = 0; i < ST_NUM && i < n; i++) {
+        ms[i] = 0.0f;
+        if (g_ev_marked[i + 1]) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, g_ev[prev], g_ev[i + 1]) != cudaSuccess)
+                return ABX_ECUDA;
+            ms[i] = t;
+            prev = i + 1;
+        }
+    }
+    return ABX_OK;
+}
+
+unsigned long long abx_launch_count(void) { return g_launches.load(); }
+
+abx_status abx_profile_counters(int64_t *out, int32_t n)
+{
+    if (!out || n < 1)
+        return ABX_EINVAL;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_state || !g_prof_stream)
+        return ABX_EINVAL;
+    if (cudaStreamSynchronize(g_prof_stream) != cudaSuccess)
+        return ABX_ECUDA;
+    const State &st = *g_prof_state;
+    int64_t v[6] = {st.pad[0], st.bits, st.dense_ok, st.n_cells, st.n_leaves, st.root};
+    for (int i = 0; i < n && i < 6; i++)
+        out[i] = v[i];
     return ABX_OK;
 }
 

@@ -261,13 +261,30 @@ void stage_cluster(const Work &w, float eps, int minpts, const Params &p, int32_
     const int B = p.block;
     const int g = div_up(w.n, B);
     if (minpts <= 2) {
-        k_union<true><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent, w.core, e2, w.dev_status);
+        prof_mark(ST_COUNT, s);
+        k_union<true><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent, w.core, e2,
+                                      w.dev_status);
+        note_launch();
+        prof_mark(ST_UNION, s);
+        prof_mark(ST_BORDER, s);
         k_finalize<true><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.spts, w.parent, w.core, w.bmin, labels);
+        note_launch();
+        prof_mark(ST_FINALIZE, s);
     } else {
         k_count<<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_first, w.core, e2, minpts, w.dev_status);
-        k_union<false><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent, w.core, e2, w.dev_status);
-        k_border<<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_first, w.parent, w.core, w.bmin, e2, w.dev_status);
+        note_launch();
+        prof_mark(ST_COUNT, s);
+        k_union<false><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent, w.core, e2,
+                                       w.dev_status);
+        note_launch();
+        prof_mark(ST_UNION, s);
+        k_border<<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_first, w.parent, w.core, w.bmin, e2,
+                                 w.dev_status);
+        note_launch();
+        prof_mark(ST_BORDER, s);
         k_finalize<false><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.spts, w.parent, w.core, w.bmin, labels);
+        note_launch();
+        prof_mark(ST_FINALIZE, s);
     }
 }
 

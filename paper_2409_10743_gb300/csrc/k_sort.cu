@@ -428,23 +428,32 @@ void stage_bounds_quant(const Work &w, const float *points, float eps, const Par
     int aligned = (reinterpret_cast<uintptr_t>(points) & 15) == 0;
     k_bounds<<<grid_for(w, (3 * w.n + 3) / 4, 256), 256, 0, s>>>(points, w.n, aligned, w.st, w.dev_status);
     k_quant<<<1, 1, 0, s>>>(w.st, eps, p.dense, p.sub_bits);
+    note_launch(3);
+    prof_mark(ST_BOUNDS, s);
 }
 
 void stage_morton_sort(const Work &w, const float *points, cudaStream_t s)
 {
     k_morton<<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.keys[0]);
+    note_launch();
+    prof_mark(ST_MORTON, s);
     k_sort_plan<<<1, RADIX, 0, s>>>(w.st, w.n);
+    note_launch();
     cudaMemsetAsync(w.sort_lb, 0, (size_t)MAX_PASSES * w.sort_tiles * RADIX * sizeof(unsigned long long), s);
     const int tiles = div_up(w.n, SORT_TILE);
     for (int pass = 0; pass < MAX_PASSES; pass++)
         k_onesweep<<<tiles, SORT_THREADS, ONESWEEP_SMEM, s>>>(pass, w.keys[0], w.keys[1], w.vals[0], w.vals[1],
                                                               w.n, w.st, w.sort_lb, w.dev_status);
+    note_launch(MAX_PASSES);
+    prof_mark(ST_SORT, s);
 }
 
 void stage_gather(const Work &w, const float *points, int minpts, cudaStream_t s)
 {
     k_gather<<<grid_for(w, w.n, 256, 16), 256, 0, s>>>(points, w.n, w.st, w.vals[0], w.vals[1], w.spts, w.parent,
                                                         w.core, minpts > 2 ? w.bmin : nullptr, minpts, w.dev_status);
+    note_launch();
+    prof_mark(ST_GATHER, s);
 }
 
 void kernels_init_device()

@@ -354,12 +354,16 @@ void stage_cells_leaves(const Work &w, float eps, int minpts, const Params &p, c
     const int min_count = minpts < 2 ? 2 : minpts;
     k_dense_cells<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.n, w.st, w.cell_start, w.spts, w.cell_dense, w.cell_root,
                                                         e2, min_count);
+    note_launch(2);
+    prof_mark(ST_CELLS, s);
     LeafFlag lf{w.cell_id, w.cell_root, w.cell_dense, w.parent, w.core, w.st, p.leaf_size};
     k_flag_scan<<<scan_tiles, SCAN_THREADS, 0, s>>>(w.n, lf, w.leaf_of, w.leaf_first, &w.st->n_leaves,
                                                     &w.st->tile_ctr[MAX_PASSES + 1], w.scan_lb + w.scan_tiles,
                                                     w.dev_status, w.st, 0);
     k_leaves<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.st, w.keys[0], w.keys[1], w.spts, w.leaf_first, w.cell_id,
                                                    w.cell_dense, w.nodes, w.delta);
+    note_launch(2);
+    prof_mark(ST_LEAVES, s);
 }
 
 void stage_hierarchy(const Work &w, cudaStream_t s)
@@ -367,6 +371,8 @@ void stage_hierarchy(const Work &w, cudaStream_t s)
     cudaMemsetAsync(w.slot, 0xff, (size_t)w.n * sizeof(unsigned long long), s);
     k_build<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.st, w.delta, w.nodes, w.slot, w.right_of);
     k_ropes<<<grid_cap(w, 2 * w.n, 256), 256, 0, s>>>(w.st, w.nodes, w.right_of, w.dev_status);
+    note_launch(2);
+    prof_mark(ST_BUILD, s);
 }
 
 }  // namespace abx

@@ -55,6 +55,16 @@ void stage_cluster(const Work &w, float eps, int minpts, const Params &p, int32_
 // One-time per-device kernel attributes.
 void kernels_init_device();
 
+// Stage timers and launch accounting (profile mode records a CUDA event on the
+// launching stream at each stage boundary).
+enum Stage {
+    ST_BOUNDS = 0, ST_MORTON, ST_SORT, ST_GATHER, ST_CELLS, ST_LEAVES, ST_BUILD,
+    ST_COUNT, ST_UNION, ST_BORDER, ST_FINALIZE, ST_NUM
+};
+void prof_begin(cudaStream_t s);
+void prof_mark(int stage, cudaStream_t s);
+void note_launch(int k = 1);
+
 __host__ __device__ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace abx
