@@ -51,8 +51,8 @@ def stage_bytes(stage: str, c: dict, n: int) -> float:
         "morton": 12.0 + 8.0,                             # read xyz, write key
         "sort": 20.0 + (P - 1) * 24.0,                    # 1st pass: key in, key+idx out; then 24/pass
         "gather": 4.0 + 12.0 + 16.0 + 4.0 + 1.0,          # perm, xyz, sorted float4, parent, core
-        "cells": 8.0 + 4.0 + 1.0,                         # keys, cell id, cell flags
-        "leaves": 4.0 + 4.0 + 16.0 + per_leaf * (32.0 + 16.0 + 1.0),  # cell id, leaf id, points; leaf records
+        "cells": 8.0 + 4.0,                               # keys, dense-root preset
+        "leaves": 4.0 + 4.0 + 16.0 + per_leaf * (32.0 + 16.0 + 1.0),  # dense root, leaf id, points; leaf records
         "build": per_leaf * (32.0 + 1.0 + 32.0 + 8.0 + 4.0 + 8.0),      # leaf box, delta, node, slot, child, rope
         "count": 16.0 + 1.0,
         "union": 16.0 + 4.0 + 4.0 + 1.0 + per_leaf * 2 * 32.0,        # point, leaf id, parent, core; nodes once
@@ -275,7 +275,10 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = abx.launch_count() - launches0
-    counters = abx.profile_counters()
+    try:
+        counters = abx.profile_counters()
+    except Exception as e:  # diagnostics only; the timing stands without them
+        counters = {"error": str(e)}
     abx.profile_enable(False)
     ms = e0.elapsed_time(e1)
     st = abx.device_status()

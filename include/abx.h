@@ -148,10 +148,12 @@ abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t
 /* ---- stage timers (tracing) -------------------------------------------------- */
 
 /*
- * abx_profile_enable -- when on, every clustering call records a CUDA event on
+ * abx_profile_enable -- on = 1: every clustering call records a CUDA event on
  * its stream at each stage boundary (bounds, morton, sort, gather, cells,
- * leaves, build, count, union, border, finalize).  Meant for one call at a
- * time (benchmarks): concurrent profiled calls overwrite each other's events.
+ * leaves, build, count, union, border, finalize).  on = 2: the same, and the
+ * pair traversal also counts its work (a slower, instrumented kernel; read
+ * with abx_profile_traversal).  on = 0: off.  Meant for one call at a time
+ * (benchmarks): concurrent profiled calls overwrite each other's events.
  */
 abx_status abx_profile_enable(int32_t on);
 
@@ -169,9 +171,17 @@ abx_status abx_profile_read(float *ms, int32_t n);
 /*
  * abx_profile_counters -- facts about the most recent profiled clustering
  * call, written to out[0 .. n-1] in this order: radix passes run, Morton bits
- * per axis, dense cells on (0/1), cells, hierarchy leaves, root node.
+ * per axis, dense cells on (0/1), dense cells found, hierarchy leaves, root
+ * node.
  */
 abx_status abx_profile_counters(int64_t *out, int32_t n);
+
+/*
+ * abx_profile_traversal -- work counters of the pair traversal of the most
+ * recent call made in profile mode 2, written to out[0 .. n-1]: node visits,
+ * leaf visits, point-pair tests, unions, queries.
+ */
+abx_status abx_profile_traversal(int64_t *out, int32_t n);
 
 /* Total number of kernels this library has launched in this process. */
 unsigned long long abx_launch_count(void);

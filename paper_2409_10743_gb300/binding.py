@@ -55,6 +55,7 @@ _SIGS = {
     "abx_profile_read": (_i32, [_vp, _i32]),
     "abx_launch_count": (ctypes.c_uint64, []),
     "abx_profile_counters": (_i32, [_vp, _i32]),
+    "abx_profile_traversal": (_i32, [_vp, _i32]),
 }
 
 
@@ -155,9 +156,18 @@ def device_status(stream=None) -> int:
     return int(lib().abx_device_status(_stream(stream)))
 
 
-def profile_enable(on: bool = True) -> None:
-    """Record CUDA events at every stage boundary of each clustering call."""
-    _check(lib().abx_profile_enable(1 if on else 0), "abx_profile_enable")
+def profile_enable(on=True) -> None:
+    """Record CUDA events at every stage boundary of each clustering call
+    (on=2: also count the pair traversal's work, in a slower kernel)."""
+    _check(lib().abx_profile_enable(int(on)), "abx_profile_enable")
+
+
+def profile_traversal() -> dict:
+    """Node visits, leaf visits, point tests, unions, queries of the pair
+    traversal in the most recent profile-mode-2 call."""
+    v = np.zeros(5, dtype=np.int64)
+    _check(lib().abx_profile_traversal(v.ctypes.data, 5), "abx_profile_traversal")
+    return dict(zip(["visits", "leaves", "tests", "unions", "queries"], map(int, v)))
 
 
 def profile_read() -> dict:
@@ -174,7 +184,7 @@ def profile_counters() -> dict:
     most recent profiled call."""
     v = np.zeros(6, dtype=np.int64)
     _check(lib().abx_profile_counters(v.ctypes.data, 6), "abx_profile_counters")
-    return dict(zip(["radix_passes", "morton_bits", "dense_cells", "cells", "leaves", "root"], map(int, v)))
+    return dict(zip(["radix_passes", "morton_bits", "dense_on", "dense_cells", "leaves", "root"], map(int, v)))
 
 
 def launch_count() -> int:

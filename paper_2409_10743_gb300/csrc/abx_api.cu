@@ -46,6 +46,7 @@ static abx_status device_ctx(DeviceCtx **out)
         if (cudaDeviceGetAttribute(&c.n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return ABX_ECUDA;
         kernels_init_device();
+        tree_init_device();
         if (cudaGetLastError() != cudaSuccess)
             return ABX_ECUDA;
         c.ready = true;
@@ -76,6 +77,8 @@ static bool g_ev_ready = false;
 static bool g_ev_marked[ST_NUM + 1];
 static cudaStream_t g_prof_stream = nullptr;
 static State *g_prof_state = nullptr;  // pinned host copy of the last profiled call's state
+static unsigned long long *g_stats_dev = nullptr;   // traversal counters (mode 2)
+static unsigned long long g_stats_host[8];
 
 void note_launch(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
@@ -135,17 +138,16 @@ static void carve(Carver &c, Work &w, int64_t n)
     w.vals[0] = c.take<unsigned>(N);
     w.vals[1] = c.take<unsigned>(N);
     w.sort_lb = c.take<unsigned long long>((size_t)MAX_PASSES * w.sort_tiles * RADIX);
-    w.scan_lb = c.take<unsigned long long>(2 * w.scan_tiles);
+    w.scan_lb = c.take<unsigned long long>(w.scan_tiles);
     w.spts = c.take<float4>(N);
-    w.cell_id = c.take<int>(N);
-    w.cell_start = c.take<int>(N + 1);
-    w.cell_dense = c.take<unsigned char>(N);
-    w.cell_root = c.take<int>(N);
+    w.dense_root = c.take<int>(N);
     w.leaf_of = c.take<int>(N);
     w.leaf_first = c.take<int>(N + 1);
+    w.pdelta = c.take<unsigned char>(N);
     w.delta = c.take<unsigned char>(N);
     w.nodes = c.take<float4>(2 * (2 * N - 1));
     w.slot = c.take<unsigned long long>(N);
+    w.frontier = c.take<int4>(N);
     w.right_of = c.take<int>(N);
     w.parent = c.take<int>(N);
     w.core = c.take<unsigned char>(N);
@@ -283,7 +285,21 @@ abx_status abx_dbscan_ex(const float *points, int64_t n, float eps, int32_t minp
     work_carve(w, ws, n);
     w.n_sms = ctx->n_sms;
     w.dev_status = ctx->status;
+    w.stats = nullptr;
+    if (g_prof_on.load() == 2) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_stats_dev && cudaMalloc(&g_stats_dev, 8 * sizeof(unsigned long long)) != cudaSuccess) {
+            g_stats_dev = nullptr;
+            cudaGetLastError();
+        }
+        if (g_stats_dev) {
+            cudaMemsetAsync(g_stats_dev, 0, 8 * sizeof(unsigned long long), s);
+            w.stats = g_stats_dev;
+        }
+    }
     run_pipeline(w, points, eps, minpts, labels, p, s);
+    if (w.stats)
+        cudaMemcpyAsync(g_stats_host, g_stats_dev, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(ws, s);
     return cuda_status(e);
@@ -354,7 +370,9 @@ static const char *k_stage_names[ST_NUM] = {"bounds", "morton", "sort", "gather"
 
 abx_status abx_profile_enable(int32_t on)
 {
-    g_prof_on.store(on ? 1 : 0);
+    if (on < 0 || on > 2)
+        return ABX_EINVAL;
+    g_prof_on.store(on);
     return ABX_OK;
 }
 
@@ -387,12 +405,26 @@ abx_status abx_profile_read(float *ms, int32_t n)
 
 unsigned long long abx_launch_count(void) { return g_launches.load(); }
 
+abx_status abx_profile_traversal(int64_t *out, int32_t n)
+{
+    if (!out || n < 1)
+        return ABX_EINVAL;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_stats_dev || !g_ev_marked[0])
+        return ABX_EINVAL;
+    if (cudaStreamSynchronize(g_prof_stream) != cudaSuccess)
+        return ABX_ECUDA;
+    for (int i = 0; i < n && i < 5; i++)
+        out[i] = (int64_t)g_stats_host[i];
+    return ABX_OK;
+}
+
 abx_status abx_profile_counters(int64_t *out, int32_t n)
 {
     if (!out || n < 1)
         return ABX_EINVAL;
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_state || !g_prof_stream)
+    if (!g_prof_state || !g_ev_marked[0])  // the stream itself may be the NULL default stream
         return ABX_EINVAL;
     if (cudaStreamSynchronize(g_prof_stream) != cudaSuccess)
         return ABX_ECUDA;

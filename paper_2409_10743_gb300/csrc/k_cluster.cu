@@ -44,11 +44,18 @@ __device__ __forceinline__ float4 node_hi(const Tree &t, int i) { return __ldg(t
 // FoF (minPts <= 2): every neighbour pair is merged and both ends become core.
 // DBSCAN (minPts > 2): only core threads run, and only core-core pairs merge.
 
-template <bool FOF>
-__global__ void k_union(int64_t n, const State *__restrict__ st,
-                                               const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
-                                               const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
-                                               int *parent, unsigned char *core, float e2, unsigned *dev_status)
+// Traversal statistics (profile mode 2 only, a separate template instance so
+// the timed kernel carries no counters): node visits, leaf visits, point
+// tests and unions, summed over all threads of the launch.
+struct TravStats {
+    unsigned long long visits, leaves, tests, unions, queries;
+};
+
+template <bool FOF, bool STATS>
+__global__ void k_union(int64_t n, const State *__restrict__ st, const float4 *__restrict__ spts,
+                        const float4 *__restrict__ nodes, const int *__restrict__ leaf_of,
+                        const int *__restrict__ leaf_first, int *parent, unsigned char *core, float e2,
+                        unsigned *dev_status, TravStats *stats)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i64 >= n)
@@ -60,6 +67,7 @@ __global__ void k_union(int64_t n, const State *__restrict__ st,
     const int L = T.L;
     const float4 p = spts[i];
     bool found = false;
+    unsigned c_visit = 0, c_leaf = 0, c_test = 0, c_union = 0;
 
     const int my_leaf = L - 1 + leaf_of[i];
     const unsigned w0 = __float_as_uint(node_lo(T, my_leaf).w);
@@ -67,8 +75,12 @@ __global__ void k_union(int64_t n, const State *__restrict__ st,
         const int e = leaf_first[my_leaf - (L - 1) + 1];
         for (int j = i + 1; j < e; j++) {
             float4 q = __ldg(spts + j);
+            if (STATS)
+                c_test++;
             if ((FOF || core[j]) && dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
                 uf_unite(parent, spts, i, j);
+                if (STATS)
+                    c_union++;
                 if (FOF) {
                     found = true;
                     core[j] = 1;
@@ -82,11 +94,15 @@ __global__ void k_union(int64_t n, const State *__restrict__ st,
         if (!node_ok(node, L, steps, dev_status))
             break;
         const float4 lo = node_lo(T, node), hi = node_hi(T, node);
+        if (STATS)
+            c_visit++;
         if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2) {
             if (node < L - 1) {
                 node = __float_as_int(lo.w);
                 continue;
             }
+            if (STATS)
+                c_leaf++;
             const unsigned lw = __float_as_uint(lo.w);
             const int s = (int)(lw & ~DENSE_BIT);
             const int e = leaf_first[node - (L - 1) + 1];
@@ -98,8 +114,12 @@ __global__ void k_union(int64_t n, const State *__restrict__ st,
                 } else {
                     for (int j = s; j < e; j++) {
                         float4 q = __ldg(spts + j);
+                        if (STATS)
+                            c_test++;
                         if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
                             uf_unite(parent, spts, i, s);
+                            if (STATS)
+                                c_union++;
                             found = true;
                             break;
                         }
@@ -108,8 +128,12 @@ __global__ void k_union(int64_t n, const State *__restrict__ st,
             } else {
                 for (int j = s; j < e; j++) {
                     float4 q = __ldg(spts + j);
+                    if (STATS)
+                        c_test++;
                     if ((FOF || core[j]) && dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
                         uf_unite(parent, spts, i, j);
+                        if (STATS)
+                            c_union++;
                         if (FOF) {
                             found = true;
                             core[j] = 1;
@@ -122,6 +146,13 @@ __global__ void k_union(int64_t n, const State *__restrict__ st,
     }
     if (FOF && found)
         core[i] = 1;
+    if (STATS) {
+        atomicAdd(&stats->visits, (unsigned long long)c_visit);
+        atomicAdd(&stats->leaves, (unsigned long long)c_leaf);
+        atomicAdd(&stats->tests, (unsigned long long)c_test);
+        atomicAdd(&stats->unions, (unsigned long long)c_union);
+        atomicAdd(&stats->queries, 1ull);
+    }
 }
 
 // ---- core counting with early termination (minPts > 2) -------------------------------
@@ -250,23 +281,27 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t n, const float4 *__res
         if (r != i)
             lab = min(orig_of(spts, r), bmin[r]);
     }
+    // labels were preset to -1: only cluster members are scattered
     const int o = __float_as_int(spts[i].w);
-    if ((unsigned)o < (unsigned)n)
+    if (lab >= 0 && (unsigned)o < (unsigned)n)
         labels[o] = lab;
 }
 
 void stage_cluster(const Work &w, float eps, int minpts, const Params &p, int32_t *labels, cudaStream_t s)
 {
     const float e2 = eps * eps;
+    cudaMemsetAsync(labels, 0xff, (size_t)w.n * sizeof(int32_t), s);  // noise = -1
     const int B = p.block;
     const int g = div_up(w.n, B);
     if (minpts <= 2) {
-        prof_mark(ST_COUNT, s);
-        k_union<true><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent, w.core, e2,
-                                      w.dev_status);
+        if (w.stats)
+            k_union<true, true><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent,
+                                                w.core, e2, w.dev_status, (TravStats *)w.stats);
+        else
+            k_union<true, false><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent,
+                                                 w.core, e2, w.dev_status, nullptr);
         note_launch();
         prof_mark(ST_UNION, s);
-        prof_mark(ST_BORDER, s);
         k_finalize<true><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.spts, w.parent, w.core, w.bmin, labels);
         note_launch();
         prof_mark(ST_FINALIZE, s);
@@ -274,8 +309,12 @@ void stage_cluster(const Work &w, float eps, int minpts, const Params &p, int32_
         k_count<<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_first, w.core, e2, minpts, w.dev_status);
         note_launch();
         prof_mark(ST_COUNT, s);
-        k_union<false><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent, w.core, e2,
-                                       w.dev_status);
+        if (w.stats)
+            k_union<false, true><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent,
+                                                 w.core, e2, w.dev_status, (TravStats *)w.stats);
+        else
+            k_union<false, false><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent,
+                                                  w.core, e2, w.dev_status, nullptr);
         note_launch();
         prof_mark(ST_UNION, s);
         k_border<<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_first, w.parent, w.core, w.bmin, e2,

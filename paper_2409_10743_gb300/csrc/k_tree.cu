@@ -138,86 +138,120 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_flag_scan(int64_t n, F f, int 
     }
 }
 
-// cell boundary: the Morton prefix above the sub-cell bits changes
-struct CellFlag {
-    const unsigned long long *k0, *k1;
-    const State *st;
-    __device__ bool operator()(int64_t k) const
-    {
-        const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
-                                                     const_cast<unsigned long long *>(k1));
-        if (k == 0)
-            return true;
-        int sh = 3 * st->sub;
-        return (keys[k] >> sh) != (keys[k - 1] >> sh);
-    }
-};
-
-// leaf boundary: a dense cell starts, the point after a dense cell, or every
-// leaf_size points within a run of non-dense points; also applies the dense
-// cells to the union-find (every member hooked under the cell's root) and
-// marks their points core.
+// Leaves are whole subtrees of the point-level radix tree (the tree the
+// build would make with one point per leaf): for a point k outside dense
+// cells, its leaf is the highest subtree containing k that holds at most
+// leaf_size points and no dense-cell point; a dense cell (itself such a
+// subtree: one Morton prefix) is one leaf.  Cutting at arbitrary multiples of
+// leaf_size instead lets leaves straddle Z-curve jumps, whose boxes then
+// inflate every ancestor box.  The climb follows the same parent rule as the
+// build (merge across the boundary with the lower split level; ties merge
+// left), finding each sibling's extent by scanning the split levels, and
+// stops as soon as the merged subtree would be too large or touch a dense cell.
+// Side effects for dense points: hooked under the cell's root, marked core.
 struct LeafFlag {
-    const int *cell_id, *cell_root;
-    const unsigned char *cell_dense;
+    const int *dense_root;
+    const unsigned char *pdelta;  // split level between sorted points k and k+1
     int *parent;
     unsigned char *core;
     const State *st;
     int leaf_size;
-    __device__ bool operator()(int64_t k) const
+    int64_t n;
+    __device__ bool has_dense(int a, int b) const
     {
-        if (!st->dense_ok)
-            return (k % leaf_size) == 0;
-        int c = cell_id[k];
-        if (cell_dense[c]) {
-            core[k] = 1;
-            int r = cell_root[c];
-            if (r != (int)k)
-                parent[k] = r;
-            return k == 0 || cell_id[k - 1] != c;
+        for (int y = a; y <= b; y++)
+            if (dense_root[y] >= 0)
+                return true;
+        return false;
+    }
+    __device__ bool operator()(int64_t k64) const
+    {
+        const int k = (int)k64;
+        const bool dok = st->dense_ok;
+        if (dok) {
+            const int r = dense_root[k];
+            if (r >= 0) {
+                core[k] = 1;
+                if (r != k)
+                    parent[k] = r;
+                return k == 0 || dense_root[k - 1] != r;
+            }
         }
-        if (k == 0)
-            return true;
-        int cp = cell_id[k - 1];
-        if (cp != c && cell_dense[cp])
-            return true;
-        return (k % leaf_size) == 0;
+        const int B = leaf_size, last = (int)n - 1;
+        int l = k, r = k;
+        while (!(l == 0 && r == last)) {
+            const bool right = (l == 0) || (r != last && pdelta[r] < pdelta[l - 1]);
+            int nl = l, nr = r;
+            if (right) {
+                const int d = pdelta[r];
+                int x = r + 1;
+                while (x < last && pdelta[x] < d && x - l + 1 <= B)
+                    x++;
+                nr = x;
+                if (nr - nl + 1 > B || (dok && has_dense(r + 1, nr)))
+                    break;
+            } else {
+                const int d = pdelta[l - 1];
+                int x = l - 2;
+                while (x >= 0 && pdelta[x] <= d && r - x <= B)
+                    x--;
+                nl = x + 1;
+                if (nr - nl + 1 > B || (dok && has_dense(nl, l - 1)))
+                    break;
+            }
+            l = nl;
+            r = nr;
+        }
+        return l == k;
     }
 };
 
-// ---- dense cells ------------------------------------------------------------------
+// ---- dense cells (one pass, no scan) ---------------------------------------------
+// The thread at the first point of each cell (a run of equal Morton prefix)
+// walks the run; a run with at least min_count points whose point box passes
+// the rounded predicate is dense: every member gets the member with the
+// smallest original index as dense_root (else dense_root stays -1).
 
-__global__ void __launch_bounds__(256) k_dense_cells(int64_t n, const State *st, const int *cell_start,
-                                                     const float4 *__restrict__ spts, unsigned char *cell_dense,
-                                                     int *cell_root, float e2, int min_count)
+__global__ void __launch_bounds__(256) k_dense_cells(int64_t n, State *st, const unsigned long long *k0,
+                                                     const unsigned long long *k1,
+                                                     const float4 *__restrict__ spts, int *dense_root, float e2,
+                                                     int min_count)
 {
     if (!st->dense_ok)
         return;
-    const int nc = st->n_cells;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        int s = cell_start[c], e = cell_start[c + 1];
-        unsigned char dense = 0;
-        if (e - s >= min_count) {
-            float4 p = spts[s];
-            float lx = p.x, ly = p.y, lz = p.z, hx = p.x, hy = p.y, hz = p.z;
-            int best = __float_as_int(p.w), root = s;
-            for (int j = s + 1; j < e; j++) {
-                float4 q = spts[j];
-                lx = fminf(lx, q.x); ly = fminf(ly, q.y); lz = fminf(lz, q.z);
-                hx = fmaxf(hx, q.x); hy = fmaxf(hy, q.y); hz = fmaxf(hz, q.z);
-                int o = __float_as_int(q.w);
-                if (o < best) {
-                    best = o;
-                    root = j;
-                }
-            }
-            // every pair of points in the box passes the rounded predicate
-            if (dist2_rn(hx, hy, hz, lx, ly, lz) <= e2) {
-                dense = 1;
-                cell_root[c] = root;
+    const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
+                                                 const_cast<unsigned long long *>(k1));
+    const int sh = 3 * st->sub;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long c = keys[k] >> sh;
+        if (k > 0 && (keys[k - 1] >> sh) == c)
+            continue;  // not the first point of its cell
+        int64_t e = k + 1;
+        while (e < n && (keys[e] >> sh) == c && e - k < min_count)
+            e++;
+        if (e - k < min_count)
+            continue;
+        while (e < n && (keys[e] >> sh) == c)
+            e++;
+        float4 p = spts[k];
+        float lx = p.x, ly = p.y, lz = p.z, hx = p.x, hy = p.y, hz = p.z;
+        int best = __float_as_int(p.w), root = (int)k;
+        for (int64_t j = k + 1; j < e; j++) {
+            float4 q = spts[j];
+            lx = fminf(lx, q.x); ly = fminf(ly, q.y); lz = fminf(lz, q.z);
+            hx = fmaxf(hx, q.x); hy = fmaxf(hy, q.y); hz = fmaxf(hz, q.z);
+            int o = __float_as_int(q.w);
+            if (o < best) {
+                best = o;
+                root = (int)j;
             }
         }
-        cell_dense[c] = dense;
+        // every pair of points in the box passes the rounded predicate
+        if (dist2_rn(hx, hy, hz, lx, ly, lz) <= e2) {
+            for (int64_t j = k; j < e; j++)
+                dense_root[j] = root;
+            atomicAdd(&st->n_cells, 1);
+        }
     }
 }
 
@@ -233,15 +267,20 @@ __device__ __forceinline__ unsigned char split_level(unsigned long long a, unsig
     return (unsigned char)(32 - __clz(t ^ (t + 1)));
 }
 
-__global__ void __launch_bounds__(256) k_leaves(const State *st, const unsigned long long *k0,
-                                                const unsigned long long *k1, const float4 *__restrict__ spts,
-                                                const int *leaf_first, const int *cell_id,
-                                                const unsigned char *cell_dense, float4 *nodes,
-                                                unsigned char *delta)
+__global__ void __launch_bounds__(256) k_pdelta(int64_t n, const State *st, const unsigned long long *k0,
+                                                const unsigned long long *k1, unsigned char *pdelta)
 {
-    const int L = st->n_leaves;
     const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
                                                  const_cast<unsigned long long *>(k1));
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n - 1; k += (int64_t)gridDim.x * blockDim.x)
+        pdelta[k] = split_level(keys[k], keys[k + 1], (int)k);
+}
+
+__global__ void __launch_bounds__(256) k_leaves(const State *st, const unsigned char *__restrict__ pdelta,
+                                                const float4 *__restrict__ spts, const int *leaf_first,
+                                                const int *dense_root, float4 *nodes, unsigned char *delta)
+{
+    const int L = st->n_leaves;
     const int dense_ok = st->dense_ok;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L; t += gridDim.x * blockDim.x) {
         int s = leaf_first[t], e = leaf_first[t + 1];
@@ -253,59 +292,161 @@ __global__ void __launch_bounds__(256) k_leaves(const State *st, const unsigned 
             hx = fmaxf(hx, q.x); hy = fmaxf(hy, q.y); hz = fmaxf(hz, q.z);
         }
         unsigned w0 = (unsigned)s;
-        if (dense_ok && cell_dense[cell_id[s]])
+        if (dense_ok && dense_root[s] >= 0)
             w0 |= DENSE_BIT;
         size_t r = 2 * ((size_t)(L - 1) + t);
         nodes[r] = make_float4(lx, ly, lz, __uint_as_float(w0));
         nodes[r + 1] = make_float4(hx, hy, hz, __int_as_float(SENTINEL));
         if (t < L - 1)
-            delta[t] = split_level(keys[e - 1], keys[e], t);
+            delta[t] = pdelta[e - 1];  // the point-level split level at the leaf boundary
     }
 }
 
-// ---- bottom-up build (one thread per leaf climbs while it arrives second) -----------
+// ---- bottom-up build -----------------------------------------------------------------
 // A node covering leaves [l, r] becomes the left child of internal node r when
 // l == 0 or delta[r] < delta[l-1] (r < L-1), else the right child of node l-1.
-// The first of two children to arrive parks (its node, its outer bound) in the
-// parent's slot and stops; the second merges the boxes and goes on.
+// Of the two children of a node, the first to arrive parks (its node id and
+// its outer bound) in the parent's slot and stops; the second merges the boxes,
+// writes the parent and climbs on.
+//
+// Phase 1 (one block per chunk of BUILD_CHUNK consecutive leaves): parents
+// whose split lies inside the chunk meet in shared memory, so most of the tree
+// is built without global atomics.  A node whose parent split is outside the
+// chunk, or that is still parked when the block ends (its sibling reaches
+// outside the chunk), is appended to a frontier list.
+// Phase 2 (global): the frontier nodes climb the rest of the way, meeting in
+// global slots through acquire-release exchanges.
 
 constexpr unsigned long long SLOT_EMPTY = ~0ull;
+constexpr unsigned long long SLOT_DONE = ~1ull;
+constexpr int BUILD_CHUNK = 1024;
 
-__global__ void __launch_bounds__(256) k_build(State *st, const unsigned char *__restrict__ delta, float4 *nodes,
-                                               unsigned long long *slot, int *right_of)
+__device__ __forceinline__ unsigned long long exch_acq_rel(unsigned long long *p, unsigned long long v)
 {
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void write_parent(float4 *nodes, int *right_of, int p, const float *b, int lc, int rc,
+                                             int r)
+{
+    // w of hi temporarily holds the range end r (turned into the rope later)
+    nodes[2 * (size_t)p] = make_float4(b[0], b[1], b[2], __int_as_float(lc));
+    nodes[2 * (size_t)p + 1] = make_float4(b[3], b[4], b[5], __int_as_float(r));
+    right_of[p] = rc;
+}
+
+__device__ __forceinline__ void push_frontier(int4 *frontier, int *count, int node, int l, int r)
+{
+    int k = atomicAdd(count, 1);
+    frontier[k] = make_int4(node, l, r, 0);
+}
+
+constexpr size_t BUILD_SMEM = (size_t)(BUILD_CHUNK - 1) * (2 * 6 * sizeof(float) + sizeof(unsigned long long));
+
+__global__ void __launch_bounds__(BUILD_CHUNK) k_build_local(State *st, const unsigned char *__restrict__ delta,
+                                                             float4 *nodes, int *right_of, int4 *frontier,
+                                                             int *frontier_count)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *stag = reinterpret_cast<unsigned long long *>(smem);
+    float *sbox = reinterpret_cast<float *>(stag + (BUILD_CHUNK - 1));  // [slot][side][6]
     const int L = st->n_leaves;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L; t += gridDim.x * blockDim.x) {
-        int node = L - 1 + t;
-        if (L == 1) {
-            st->root = node;
-            continue;
-        }
-        int l = t, r = t;
+    const int c0 = blockIdx.x * BUILD_CHUNK;
+    if (c0 >= L)
+        return;
+    for (int i = threadIdx.x; i < BUILD_CHUNK - 1; i += blockDim.x)
+        stag[i] = SLOT_EMPTY;
+    __syncthreads();
+    const int t = c0 + threadIdx.x;
+    if (t < L) {
+        int node = L - 1 + t, l = t, r = t;
         float4 lo = nodes[2 * (size_t)node], hi = nodes[2 * (size_t)node + 1];
-        while (true) {
-            bool left = (l == 0) || (r != L - 1 && delta[r] < delta[l - 1]);
-            int p = left ? r : l - 1;
-            unsigned long long mine = ((unsigned long long)(unsigned)node << 32) | (unsigned)(left ? l : r);
-            __threadfence();
-            unsigned long long other = atomicExch(slot + p, mine);
-            if (other == SLOT_EMPTY)
+        float b[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
+        if (L == 1)
+            st->root = node;
+        while (L > 1) {
+            const bool left = (l == 0) || (r != L - 1 && delta[r] < delta[l - 1]);
+            const int p = left ? r : l - 1;
+            if (p < c0 || p > c0 + BUILD_CHUNK - 2) {
+                push_frontier(frontier, frontier_count, node, l, r);
                 break;
-            __threadfence();
-            int sib = (int)(other >> 32);
-            int bound = (int)(unsigned)other;
+            }
+            const int q = p - c0, side = left ? 0 : 1;
+            float *mine = sbox + (q * 2 + side) * 6;
+#pragma unroll
+            for (int k = 0; k < 6; k++)
+                mine[k] = b[k];
+            __threadfence_block();
+            const unsigned long long tag = ((unsigned long long)(unsigned)node << 32) |
+                                           ((unsigned long long)side << 31) | (unsigned)(left ? l : r);
+            const unsigned long long other = atomicExch(stag + q, tag);
+            if (other == SLOT_EMPTY)
+                break;  // parked: the sibling will continue
+            stag[q] = SLOT_DONE;
+            __threadfence_block();
+            const int sib = (int)(other >> 32);
+            const int bound = (int)(other & 0x7fffffffu);
+            const float *theirs = sbox + (q * 2 + (1 - side)) * 6;
+            b[0] = fminf(b[0], theirs[0]); b[1] = fminf(b[1], theirs[1]); b[2] = fminf(b[2], theirs[2]);
+            b[3] = fmaxf(b[3], theirs[3]); b[4] = fmaxf(b[4], theirs[4]); b[5] = fmaxf(b[5], theirs[5]);
             if (left)
                 r = bound;
             else
                 l = bound;
-            float4 slo = ld_cg4(nodes + 2 * (size_t)sib), shi = ld_cg4(nodes + 2 * (size_t)sib + 1);
+            write_parent(nodes, right_of, p, b, left ? node : sib, left ? sib : node, r);
+            node = p;
+            if (l == 0 && r == L - 1) {
+                st->root = p;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    // nodes still parked: their sibling reaches outside the chunk
+    for (int q = threadIdx.x; q < BUILD_CHUNK - 1; q += blockDim.x) {
+        const unsigned long long tag = stag[q];
+        if (tag == SLOT_EMPTY || tag == SLOT_DONE)
+            continue;
+        const int node = (int)(tag >> 32);
+        const int bound = (int)(tag & 0x7fffffffu);
+        const int p = c0 + q;
+        if ((tag >> 31) & 1u)  // right child [p + 1, bound]
+            push_frontier(frontier, frontier_count, node, p + 1, bound);
+        else                   // left child [bound, p]
+            push_frontier(frontier, frontier_count, node, bound, p);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_build_global(State *st, const unsigned char *__restrict__ delta,
+                                                      float4 *nodes, unsigned long long *slot, int *right_of,
+                                                      const int4 *frontier, const int *frontier_count)
+{
+    const int L = st->n_leaves;
+    const int nf = *frontier_count;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+        const int4 it = frontier[f];
+        int node = it.x, l = it.y, r = it.z;
+        float4 lo = ld_cg4(nodes + 2 * (size_t)node), hi = ld_cg4(nodes + 2 * (size_t)node + 1);
+        while (true) {
+            const bool left = (l == 0) || (r != L - 1 && delta[r] < delta[l - 1]);
+            const int p = left ? r : l - 1;
+            const unsigned long long mine = ((unsigned long long)(unsigned)node << 32) | (unsigned)(left ? l : r);
+            const unsigned long long other = exch_acq_rel(slot + p, mine);
+            if (other == SLOT_EMPTY)
+                break;
+            const int sib = (int)(other >> 32);
+            const int bound = (int)(unsigned)other;
+            if (left)
+                r = bound;
+            else
+                l = bound;
+            const float4 slo = ld_cg4(nodes + 2 * (size_t)sib), shi = ld_cg4(nodes + 2 * (size_t)sib + 1);
             lo.x = fminf(lo.x, slo.x); lo.y = fminf(lo.y, slo.y); lo.z = fminf(lo.z, slo.z);
             hi.x = fmaxf(hi.x, shi.x); hi.y = fmaxf(hi.y, shi.y); hi.z = fmaxf(hi.z, shi.z);
-            int lc = left ? node : sib, rc = left ? sib : node;
-            // w of hi temporarily holds the range end r (turned into the rope later)
-            nodes[2 * (size_t)p] = make_float4(lo.x, lo.y, lo.z, __int_as_float(lc));
-            nodes[2 * (size_t)p + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(r));
-            right_of[p] = rc;
+            const float b[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
+            write_parent(nodes, right_of, p, b, left ? node : sib, left ? sib : node, r);
             node = p;
             if (l == 0 && r == L - 1) {
                 st->root = p;
@@ -346,33 +487,41 @@ static int grid_cap(const Work &w, int64_t n, int block, int per_sm = 8)
 void stage_cells_leaves(const Work &w, float eps, int minpts, const Params &p, cudaStream_t s)
 {
     const int scan_tiles = div_up(w.n, SCAN_TILE);
-    cudaMemsetAsync(w.scan_lb, 0, 2 * w.scan_tiles * sizeof(unsigned long long), s);
-    CellFlag cf{w.keys[0], w.keys[1], w.st};
-    k_flag_scan<<<scan_tiles, SCAN_THREADS, 0, s>>>(w.n, cf, w.cell_id, w.cell_start, &w.st->n_cells,
-                                                    &w.st->tile_ctr[MAX_PASSES], w.scan_lb, w.dev_status, w.st, 1);
     const float e2 = eps * eps;
     const int min_count = minpts < 2 ? 2 : minpts;
-    k_dense_cells<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.n, w.st, w.cell_start, w.spts, w.cell_dense, w.cell_root,
-                                                        e2, min_count);
-    note_launch(2);
+    cudaMemsetAsync(w.dense_root, 0xff, (size_t)w.n * sizeof(int), s);
+    k_dense_cells<<<grid_cap(w, w.n, 256, 16), 256, 0, s>>>(w.n, w.st, w.keys[0], w.keys[1], w.spts, w.dense_root,
+                                                            e2, min_count);
+    note_launch(1);
     prof_mark(ST_CELLS, s);
-    LeafFlag lf{w.cell_id, w.cell_root, w.cell_dense, w.parent, w.core, w.st, p.leaf_size};
+    k_pdelta<<<grid_cap(w, w.n, 256, 16), 256, 0, s>>>(w.n, w.st, w.keys[0], w.keys[1], w.pdelta);
+    cudaMemsetAsync(w.scan_lb, 0, w.scan_tiles * sizeof(unsigned long long), s);
+    LeafFlag lf{w.dense_root, w.pdelta, w.parent, w.core, w.st, p.leaf_size, w.n};
     k_flag_scan<<<scan_tiles, SCAN_THREADS, 0, s>>>(w.n, lf, w.leaf_of, w.leaf_first, &w.st->n_leaves,
-                                                    &w.st->tile_ctr[MAX_PASSES + 1], w.scan_lb + w.scan_tiles,
-                                                    w.dev_status, w.st, 0);
-    k_leaves<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.st, w.keys[0], w.keys[1], w.spts, w.leaf_first, w.cell_id,
-                                                   w.cell_dense, w.nodes, w.delta);
-    note_launch(2);
+                                                    &w.st->tile_ctr[MAX_PASSES + 1], w.scan_lb, w.dev_status, w.st,
+                                                    0);
+    k_leaves<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.st, w.pdelta, w.spts, w.leaf_first, w.dense_root, w.nodes,
+                                                   w.delta);
+    note_launch(3);
     prof_mark(ST_LEAVES, s);
 }
 
 void stage_hierarchy(const Work &w, cudaStream_t s)
 {
     cudaMemsetAsync(w.slot, 0xff, (size_t)w.n * sizeof(unsigned long long), s);
-    k_build<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.st, w.delta, w.nodes, w.slot, w.right_of);
+    cudaMemsetAsync(&w.st->pad[1], 0, sizeof(int), s);  // frontier count
+    k_build_local<<<div_up(w.n, BUILD_CHUNK), BUILD_CHUNK, BUILD_SMEM, s>>>(w.st, w.delta, w.nodes, w.right_of,
+                                                                            w.frontier, &w.st->pad[1]);
+    k_build_global<<<grid_cap(w, w.n / 16 + 1, 256), 256, 0, s>>>(w.st, w.delta, w.nodes, w.slot, w.right_of,
+                                                                  w.frontier, &w.st->pad[1]);
     k_ropes<<<grid_cap(w, 2 * w.n, 256), 256, 0, s>>>(w.st, w.nodes, w.right_of, w.dev_status);
-    note_launch(2);
+    note_launch(3);
     prof_mark(ST_BUILD, s);
+}
+
+void tree_init_device()
+{
+    cudaFuncSetAttribute(k_build_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BUILD_SMEM);
 }
 
 }  // namespace abx

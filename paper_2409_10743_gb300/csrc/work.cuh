@@ -22,21 +22,21 @@ struct Work {
     unsigned long long *keys[2];     // Morton keys, radix double buffer
     unsigned *vals[2];               // original indices, radix double buffer
     unsigned long long *sort_lb;     // [MAX_PASSES][tiles][RADIX] look-back words
-    unsigned long long *scan_lb;     // [2][scan tiles] look-back words
+    unsigned long long *scan_lb;     // [scan tiles] look-back words
     float4 *spts;                    // sorted points: x, y, z, original index (as int bits)
-    int *cell_id;                    // [n] cell of each sorted point
-    int *cell_start;                 // [n + 1]
-    unsigned char *cell_dense;       // [n]
-    int *cell_root;                  // [n] member with the smallest original index
+    int *dense_root;                 // [n] root of the point's dense cell, or -1
     int *leaf_of;                    // [n] leaf of each sorted point
     int *leaf_first;                 // [n + 1] first sorted point of each leaf
+    unsigned char *pdelta;           // [n] split level between sorted points k and k+1
     unsigned char *delta;            // [n] split level between leaves t and t+1
     float4 *nodes;                   // [2 * (2n - 1)] hierarchy records (lo, hi)
-    unsigned long long *slot;        // [n] bottom-up meeting slots
+    unsigned long long *slot;        // [n] bottom-up meeting slots (global phase)
+    int4 *frontier;                  // [n] nodes that finish the build in the global phase
     int *right_of;                   // [n] right child of each internal node
     int *parent;                     // [n] union-find parents (sorted positions)
     unsigned char *core;             // [n] core flags
     int *bmin;                       // [n] smallest border index per cluster root
+    unsigned long long *stats;       // traversal counters (profile mode 2) or null
     size_t sort_tiles, scan_tiles;
 };
 
@@ -54,6 +54,7 @@ void stage_cluster(const Work &w, float eps, int minpts, const Params &p, int32_
 
 // One-time per-device kernel attributes.
 void kernels_init_device();
+void tree_init_device();
 
 // Stage timers and launch accounting (profile mode records a CUDA event on the
 // launching stream at each stage boundary).

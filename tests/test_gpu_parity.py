@@ -210,3 +210,25 @@ def test_scaled_configs(abx, name):
     cfg = scaled(CONFIGS[name], 300_000)
     p = cfg.points()
     assert_same(gpu_labels(abx, p, cfg.eps, cfg.minpts), oracle.dbscan(p, cfg.eps, cfg.minpts), cfg.describe())
+
+
+def test_profile_api(abx):
+    """Stage timers, counters and the launch counter on the default stream."""
+    p = clumps(300_000, 300, 51, a0=0.02)
+    t = torch.from_numpy(p).cuda()
+    abx.profile_enable(True)
+    try:
+        n0 = abx.launch_count()
+        abx.dbscan(t, 0.004, 2)
+        ms = abx.profile_read()
+        c = abx.profile_counters()
+        n1 = abx.launch_count()
+        abx.dbscan(t, 0.004, 5)
+        ms5 = abx.profile_read()
+    finally:
+        abx.profile_enable(False)
+    assert set(ms) >= {"bounds", "sort", "union", "finalize"}
+    assert all(v >= 0 for v in ms.values()) and ms["union"] > 0 and ms["count"] == 0
+    assert ms5["count"] > 0 and ms5["border"] > 0
+    assert 1 <= c["radix_passes"] <= 8 and 1 <= c["leaves"] <= len(p) and c["morton_bits"] <= 21
+    assert n1 - n0 >= 15
