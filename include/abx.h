@@ -76,7 +76,8 @@ typedef struct CUstream_st *abx_stream;
  * changes the labels; they only change speed and memory.
  *   leaf_size    points per ordinary hierarchy leaf (1..32, default 4)
  *   dense_cells  1 = FDBSCAN-DenseBox dense-cell leaves on, -1 = off (default on)
- *   sub_bits     Morton bits per axis below the dense-cell side (0..8, default 3)
+ *   sub_bits     Morton bits per axis below the dense-cell side (1..8; -1 = none,
+ *                the default)
  *   block        threads per block of the traversal kernels (64..1024, default 256)
  */
 typedef struct abx_params {

@@ -173,7 +173,7 @@ static abx_status resolve_params(const abx_params *in, Params &p)
 {
     p.leaf_size = 4;
     p.dense = 1;
-    p.sub_bits = 3;
+    p.sub_bits = 0;
     p.block = 256;
     if (!in)
         return ABX_OK;
@@ -188,9 +188,9 @@ static abx_status resolve_params(const abx_params *in, Params &p)
         p.dense = in->dense_cells == 1;
     }
     if (in->sub_bits) {
-        if (in->sub_bits < 0 || in->sub_bits > 8)
+        if (in->sub_bits < -1 || in->sub_bits > 8)
             return ABX_EINVAL;
-        p.sub_bits = in->sub_bits;
+        p.sub_bits = in->sub_bits < 0 ? 0 : in->sub_bits;
     }
     if (in->block) {
         if (in->block < 64 || in->block > 1024 || (in->block & 31))

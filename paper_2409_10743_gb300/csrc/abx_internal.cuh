@@ -19,8 +19,8 @@ constexpr int SENTINEL = -1;        // rope of the right-most path (paper, fig. 
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int MAX_PASSES = 8;       // 64-bit keys, 8 bits per pass
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 16;
+constexpr int SORT_THREADS = 512;
+constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;

@@ -258,14 +258,13 @@ __device__ unsigned long long lookback_sum(const unsigned long long *lb, int til
     return excl;
 }
 
+constexpr int SORT_WARPS = SORT_THREADS / 32;
 constexpr size_t ONESWEEP_SMEM =
-    SORT_TILE * sizeof(unsigned long long) + SORT_TILE * sizeof(unsigned) + (SORT_THREADS / 32) * RADIX * 4 +
-    2 * RADIX * 4;
+    SORT_TILE * sizeof(unsigned long long) + SORT_TILE * sizeof(unsigned) + SORT_WARPS * RADIX * 4 + 2 * RADIX * 4;
 
-__global__ void __launch_bounds__(SORT_THREADS) k_onesweep(int pass, unsigned long long *k0,
-                                                           unsigned long long *k1, unsigned *v0, unsigned *v1,
-                                                           int64_t n, State *st, unsigned long long *lb_all,
-                                                           unsigned *dev_status)
+__global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, unsigned long long *k0, unsigned long long *k1,
+                                                              unsigned *v0, unsigned *v1, int64_t n, State *st,
+                                                              unsigned long long *lb_all, unsigned *dev_status)
 {
     const int ord = st->pass_ord[pass];
     if (ord < 0)
@@ -282,16 +281,16 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(int pass, unsigned lo
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *s_keys = reinterpret_cast<unsigned long long *>(smem);
     unsigned *s_vals = reinterpret_cast<unsigned *>(s_keys + SORT_TILE);
-    unsigned *s_whist = s_vals + SORT_TILE;          // [warps][RADIX]
-    unsigned *s_loc = s_whist + (SORT_THREADS / 32) * RADIX;  // tile-local digit offsets
-    unsigned *s_glob = s_loc + RADIX;                // destination base per digit
+    unsigned *s_whist = s_vals + SORT_TILE;      // [warps][RADIX]
+    unsigned *s_loc = s_whist + SORT_WARPS * RADIX;  // tile-local digit offsets
+    unsigned *s_glob = s_loc + RADIX;            // destination base per digit
     __shared__ int s_tile;
-    __shared__ unsigned s_wsum[SORT_THREADS / 32];
+    __shared__ unsigned s_wsum[RADIX / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0)
         s_tile = (int)atomicAdd(&st->tile_ctr[pass], 1u);
-    for (int i = tid; i < (SORT_THREADS / 32) * RADIX; i += SORT_THREADS)
+    for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS)
         s_whist[i] = 0;
     __syncthreads();
     const int tile = s_tile;
@@ -302,48 +301,50 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(int pass, unsigned lo
     unsigned rank[SORT_ITEMS];
 #pragma unroll
     for (int k = 0; k < SORT_ITEMS; k++) {
-        int64_t pos = base + k * 32;
-        if (pos < n) {
-            key[k] = ksrc[pos];
-            val[k] = first ? (unsigned)pos : vsrc[pos];
-        } else {
-            key[k] = ~0ull;  // pads rank last in digit RADIX-1 and land at >= n
-            val[k] = 0;
-        }
+        const int64_t pos = base + k * 32;
+        key[k] = pos < n ? ksrc[pos] : ~0ull;  // pads rank last in digit RADIX-1 and land at >= n
     }
+#pragma unroll
+    for (int k = 0; k < SORT_ITEMS; k++) {
+        const int64_t pos = base + k * 32;
+        val[k] = pos < n ? (first ? (unsigned)pos : vsrc[pos]) : 0u;
+    }
+    // stable rank within the warp: lanes with equal digit, in lane order, after
+    // the earlier items of this warp
     unsigned *wh = s_whist + warp * RADIX;
     const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int k = 0; k < SORT_ITEMS; k++) {
-        unsigned d = (unsigned)(key[k] >> shift) & (RADIX - 1);
-        unsigned peers = __match_any_sync(~0u, d);
-        unsigned before = __popc(peers & lt_mask);
-        unsigned prev = wh[d];
-        rank[k] = prev + before;
-        __syncwarp();
-        if (before == 0)
-            wh[d] = prev + __popc(peers);
-        __syncwarp();
+        const unsigned d = (unsigned)(key[k] >> shift) & (RADIX - 1);
+        const unsigned peers = __match_any_sync(~0u, d);
+        const int leader = __ffs(peers) - 1;
+        unsigned prev = 0;
+        if (lane == leader)
+            prev = atomicAdd(wh + d, (unsigned)__popc(peers));
+        prev = __shfl_sync(~0u, prev, leader);
+        rank[k] = prev + __popc(peers & lt_mask);
     }
     __syncthreads();
 
-    // thread d: per-warp exclusive offsets and the tile count of digit d
-    const int d = tid;
+    // thread d < RADIX: per-warp exclusive offsets and the tile count of digit d
     unsigned cnt = 0;
-#pragma unroll
-    for (int w = 0; w < SORT_THREADS / 32; w++) {
-        unsigned c = s_whist[w * RADIX + d];
-        s_whist[w * RADIX + d] = cnt;
-        cnt += c;
-    }
-    // publish, then look back
     unsigned long long excl = 0;
-    if (tile == 0) {
-        st_relaxed_u64(lb + d, LB_PRE | cnt);
-    } else {
-        st_relaxed_u64(lb + (size_t)tile * RADIX + d, LB_AGG | cnt);
-        excl = lookback_sum(lb, tile, RADIX, d, dev_status);
-        st_relaxed_u64(lb + (size_t)tile * RADIX + d, LB_PRE | (excl + cnt));
+    if (tid < RADIX) {
+        const int d = tid;
+#pragma unroll
+        for (int w = 0; w < SORT_WARPS; w++) {
+            unsigned c = s_whist[w * RADIX + d];
+            s_whist[w * RADIX + d] = cnt;
+            cnt += c;
+        }
+        // publish, then look back
+        if (tile == 0) {
+            st_relaxed_u64(lb + d, LB_PRE | cnt);
+        } else {
+            st_relaxed_u64(lb + (size_t)tile * RADIX + d, LB_AGG | cnt);
+            excl = lookback_sum(lb, tile, RADIX, d, dev_status);
+            st_relaxed_u64(lb + (size_t)tile * RADIX + d, LB_PRE | (excl + cnt));
+        }
     }
     // exclusive scan of cnt over digits (tile-local offsets)
     unsigned x = cnt;
@@ -353,29 +354,32 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(int pass, unsigned lo
         if (lane >= o)
             x += y;
     }
-    if (lane == 31)
+    if (tid < RADIX && lane == 31)
         s_wsum[warp] = x;
     __syncthreads();
-    unsigned wpre = 0;
-    for (int w = 0; w < warp; w++)
-        wpre += s_wsum[w];
-    const unsigned loc = wpre + x - cnt;
-    s_loc[d] = loc;
-    s_glob[d] = st->hist[pass][d] + (unsigned)excl - loc;
+    if (tid < RADIX) {
+        unsigned wpre = 0;
+        for (int w = 0; w < warp; w++)
+            wpre += s_wsum[w];
+        const unsigned loc = wpre + x - cnt;
+        s_loc[tid] = loc;
+        s_glob[tid] = st->hist[pass][tid] + (unsigned)excl - loc;
+    }
     __syncthreads();
 
 #pragma unroll
     for (int k = 0; k < SORT_ITEMS; k++) {
-        unsigned dd = (unsigned)(key[k] >> shift) & (RADIX - 1);
-        unsigned lp = s_loc[dd] + s_whist[warp * RADIX + dd] + rank[k];
+        const unsigned dd = (unsigned)(key[k] >> shift) & (RADIX - 1);
+        const unsigned lp = s_loc[dd] + s_whist[warp * RADIX + dd] + rank[k];
         s_keys[lp] = key[k];
         s_vals[lp] = val[k];
     }
     __syncthreads();
+#pragma unroll 4
     for (int i = tid; i < SORT_TILE; i += SORT_THREADS) {
-        unsigned long long kk = s_keys[i];
-        unsigned dd = (unsigned)(kk >> shift) & (RADIX - 1);
-        unsigned dest = s_glob[dd] + (unsigned)i;
+        const unsigned long long kk = s_keys[i];
+        const unsigned dd = (unsigned)(kk >> shift) & (RADIX - 1);
+        const unsigned dest = s_glob[dd] + (unsigned)i;
         if ((int64_t)dest < n) {
             kdst[dest] = kk;
             vdst[dest] = s_vals[i];

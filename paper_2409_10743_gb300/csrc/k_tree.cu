@@ -139,15 +139,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_flag_scan(int64_t n, F f, int 
 }
 
 // Leaves are whole subtrees of the point-level radix tree (the tree the
-// build would make with one point per leaf): for a point k outside dense
-// cells, its leaf is the highest subtree containing k that holds at most
-// leaf_size points and no dense-cell point; a dense cell (itself such a
-// subtree: one Morton prefix) is one leaf.  Cutting at arbitrary multiples of
-// leaf_size instead lets leaves straddle Z-curve jumps, whose boxes then
-// inflate every ancestor box.  The climb follows the same parent rule as the
-// build (merge across the boundary with the lower split level; ties merge
-// left), finding each sibling's extent by scanning the split levels, and
-// stops as soon as the merged subtree would be too large or touch a dense cell.
+// build would make with one point per leaf): for a point outside dense cells
+// its leaf is the highest subtree containing it that holds at most leaf_size
+// points and no dense-cell point; a dense cell (itself such a subtree: one
+// Morton prefix) is one leaf.  Cutting at arbitrary multiples of leaf_size
+// instead lets leaves straddle Z-curve jumps, whose boxes then inflate every
+// ancestor box.
+//
+// The boundary x between sorted points x and x+1 is the split of exactly one
+// internal node, whose points run from just after the nearest boundary on the
+// left with a higher split level to the nearest boundary on the right with an
+// equal or higher one (the build's parent rule: merge across the lower level,
+// ties merge left).  x is inside a leaf iff that node holds at most leaf_size
+// points and no dense point; so only 2 * leaf_size split levels are read.
 // Side effects for dense points: hooked under the cell's root, marked core.
 struct LeafFlag {
     const int *dense_root;
@@ -157,52 +161,42 @@ struct LeafFlag {
     const State *st;
     int leaf_size;
     int64_t n;
-    __device__ bool has_dense(int a, int b) const
-    {
-        for (int y = a; y <= b; y++)
-            if (dense_root[y] >= 0)
-                return true;
-        return false;
-    }
     __device__ bool operator()(int64_t k64) const
     {
         const int k = (int)k64;
         const bool dok = st->dense_ok;
         if (dok) {
-            const int r = dense_root[k];
-            if (r >= 0) {
+            const int rb = dense_root[k];
+            if (rb >= 0) {
                 core[k] = 1;
-                if (r != k)
-                    parent[k] = r;
-                return k == 0 || dense_root[k - 1] != r;
+                if (rb != k)
+                    parent[k] = rb;
+                return k == 0 || dense_root[k - 1] != rb;
             }
+            if (k > 0 && dense_root[k - 1] >= 0)
+                return true;  // first point after a dense cell
         }
-        const int B = leaf_size, last = (int)n - 1;
-        int l = k, r = k;
-        while (!(l == 0 && r == last)) {
-            const bool right = (l == 0) || (r != last && pdelta[r] < pdelta[l - 1]);
-            int nl = l, nr = r;
-            if (right) {
-                const int d = pdelta[r];
-                int x = r + 1;
-                while (x < last && pdelta[x] < d && x - l + 1 <= B)
-                    x++;
-                nr = x;
-                if (nr - nl + 1 > B || (dok && has_dense(r + 1, nr)))
-                    break;
-            } else {
-                const int d = pdelta[l - 1];
-                int x = l - 2;
-                while (x >= 0 && pdelta[x] <= d && r - x <= B)
-                    x--;
-                nl = x + 1;
-                if (nr - nl + 1 > B || (dok && has_dense(nl, l - 1)))
-                    break;
-            }
-            l = nl;
-            r = nr;
+        if (k == 0)
+            return true;
+        const int x = k - 1, B = leaf_size, last = (int)n - 1;
+        const int d = pdelta[x];
+        int yr = x + 1;  // nearest boundary on the right with level >= d
+        while (yr < last && pdelta[yr] < d) {
+            if (++yr - x > B)
+                return true;
         }
-        return l == k;
+        int yl = x - 1;  // nearest boundary on the left with level > d
+        while (yl >= 0 && pdelta[yl] <= d) {
+            if (x - --yl > B)
+                return true;
+        }
+        if (yr - yl > B)  // the node holds points yl + 1 .. yr
+            return true;
+        if (dok)
+            for (int y = yl + 1; y <= yr; y++)
+                if (dense_root[y] >= 0)
+                    return true;
+        return false;
     }
 };
 

@@ -54,7 +54,7 @@ def test_small_cases(abx, case):
 
 
 PARAMS = [dict(leaf_size=1), dict(leaf_size=2), dict(leaf_size=8), dict(leaf_size=32),
-          dict(dense_cells=-1), dict(sub_bits=0), dict(sub_bits=8), dict(block=128),
+          dict(dense_cells=-1), dict(sub_bits=3), dict(sub_bits=8), dict(block=128),
           dict(block=1024), dict(leaf_size=1, dense_cells=-1)]
 
 
