@@ -146,6 +146,27 @@ abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t
                             const float *eps, const int32_t *minpts, int32_t *labels,
                             abx_stream stream);
 
+/*
+ * abx_dbscan_noalloc -- abx_dbscan for callers that cannot allocate device
+ * memory (an in-situ hook inside a simulation that has reserved the GPU's
+ * memory for itself, or code where allocation calls are not permitted).  The
+ * paper has no counterpart: this is a deployment variant of the same
+ * clustering, with the same labels.
+ *   points, eps, minpts, labels, stream: as for abx_dbscan
+ *   n       0 <= n <= 65536; larger inputs return ABX_EINVAL before anything
+ *           is enqueued
+ * Calls no allocation routine.  The workspace is a fixed array of device
+ * memory (12 MiB per device that loads the library, held until
+ * the process exits).  The first call on a device looks up that array's
+ * address and sets kernel attributes; make that first call before any stream
+ * capture.  Every call on a device shares the array: calls whose work
+ * overlaps on the GPU race, so serialise them (one stream, one at a time).
+ * Device-side error flags of this entry point are kept apart and are not
+ * reported by abx_device_status: pass finite coordinates.
+ */
+abx_status abx_dbscan_noalloc(const float *points, int64_t n, float eps, int32_t minpts,
+                              int32_t *labels, abx_stream stream);
+
 /* ---- stage timers (tracing) -------------------------------------------------- */
 
 /*
