@@ -126,10 +126,16 @@ struct Carver {
     }
 };
 
-static void carve(Carver &c, Work &w, int64_t n)
+static void carve(Carver &c, Work &w, int64_t n, int nseg)
 {
     const size_t N = (size_t)n;
     w.n = n;
+    w.nseg = nseg;
+    w.seg_off = c.take<int>((size_t)nseg + 1);
+    w.seg = c.take<SegState>((size_t)nseg);
+    w.seg_eps_in = c.take<float>((size_t)nseg);
+    w.seg_minpts_in = c.take<int>((size_t)nseg);
+    w.leaf_seg = c.take<int>(N);
     w.sort_tiles = (size_t)div_up(n, SORT_TILE);
     w.scan_tiles = (size_t)div_up(n, SCAN_TILE);
     w.st = c.take<State>(1);
@@ -154,19 +160,21 @@ static void carve(Carver &c, Work &w, int64_t n)
     w.bmin = c.take<int>(N);
 }
 
-size_t work_bytes(int64_t n)
+size_t work_bytes(int64_t n, int nseg)
 {
     Carver c;
     Work w;
-    carve(c, w, n);
+    carve(c, w, n, nseg);
     return c.off;
 }
 
-void work_carve(Work &w, void *base, int64_t n)
+void work_carve(Work &w, void *base, int64_t n, int nseg)
 {
     Carver c;
     c.base = static_cast<char *>(base);
-    carve(c, w, n);
+    carve(c, w, n, nseg);
+    w.stats = nullptr;
+    w.any_fof = w.any_dbscan = false;
 }
 
 static abx_status resolve_params(const abx_params *in, Params &p)
@@ -207,17 +215,16 @@ static abx_status cuda_status(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? ABX_ENOMEM : ABX_ECUDA;
 }
 
-// Enqueue the whole pipeline on `s` over a carved workspace.
-static void run_pipeline(Work &w, const float *points, float eps, int minpts, int32_t *labels, const Params &p,
-                         cudaStream_t s)
+// Enqueue the whole pipeline on `s` over a carved workspace whose segment
+// parameters are set up (or about to be, earlier on the same stream).
+static void run_stages(Work &w, const float *points, int32_t *labels, const Params &p, cudaStream_t s)
 {
-    prof_begin(s);
-    stage_bounds_quant(w, points, eps, p, s);
+    stage_bounds_quant(w, points, p, s);
     stage_morton_sort(w, points, s);
-    stage_gather(w, points, minpts, s);
-    stage_cells_leaves(w, eps, minpts, p, s);
+    stage_gather(w, points, s);
+    stage_cells_leaves(w, p, s);
     stage_hierarchy(w, s);
-    stage_cluster(w, eps, minpts, p, labels, s);
+    stage_cluster(w, p, labels, s);
     if (g_prof_on.load()) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         if (!g_prof_state && cudaMallocHost((void **)&g_prof_state, sizeof(State)) != cudaSuccess) {
@@ -282,10 +289,11 @@ abx_status abx_dbscan_ex(const float *points, int64_t n, float eps, int32_t minp
         return ABX_ENOMEM;
     }
     Work w;
-    work_carve(w, ws, n);
+    work_carve(w, ws, n, 1);
     w.n_sms = ctx->n_sms;
     w.dev_status = ctx->status;
-    w.stats = nullptr;
+    w.any_fof = minpts <= 2;
+    w.any_dbscan = !w.any_fof;
     if (g_prof_on.load() == 2) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         if (!g_stats_dev && cudaMalloc(&g_stats_dev, 8 * sizeof(unsigned long long)) != cudaSuccess) {
@@ -297,7 +305,9 @@ abx_status abx_dbscan_ex(const float *points, int64_t n, float eps, int32_t minp
             w.stats = g_stats_dev;
         }
     }
-    run_pipeline(w, points, eps, minpts, labels, p, s);
+    prof_begin(s);
+    stage_segments_single(w, eps, minpts, s);
+    run_stages(w, points, labels, p, s);
     if (w.stats)
         cudaMemcpyAsync(g_stats_host, g_stats_dev, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaGetLastError();
@@ -429,7 +439,7 @@ abx_status abx_profile_counters(int64_t *out, int32_t n)
     if (cudaStreamSynchronize(g_prof_stream) != cudaSuccess)
         return ABX_ECUDA;
     const State &st = *g_prof_state;
-    int64_t v[6] = {st.pad[0], st.bits, st.dense_ok, st.n_cells, st.n_leaves, st.root};
+    int64_t v[6] = {st.n_active, st.bits, st.dense_ok, st.n_cells, st.n_leaves, st.root};
     for (int i = 0; i < n && i < 6; i++)
         out[i] = v[i];
     return ABX_OK;
@@ -451,15 +461,50 @@ abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t
         if (rc != ABX_OK)
             return rc;
     }
-    if (offsets[nseg] > INT32_MAX)
+    const int64_t n = offsets[nseg];
+    if (n > INT32_MAX || nseg > (1 << 24))
         return ABX_EINVAL;
-    for (int32_t k = 0; k < nseg; k++) {
-        int64_t a = offsets[k], m = offsets[k + 1] - a;
-        abx_status rc = abx_dbscan(points + 3 * a, m, eps[k], minpts[k], labels + a, stream);
-        if (rc != ABX_OK)
-            return rc;
+    if (n == 0)
+        return ABX_OK;
+    if (nseg == 1)
+        return abx_dbscan(points, n, eps[0], minpts[0], labels, stream);
+    DeviceCtx *ctx;
+    abx_status rc = device_ctx(&ctx);
+    if (rc != ABX_OK)
+        return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    if (cudaMallocFromPoolAsync(&ws, work_bytes(n, nseg), ctx->pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return ABX_ENOMEM;
     }
-    return ABX_OK;
+    Work w;
+    work_carve(w, ws, n, nseg);
+    w.n_sms = ctx->n_sms;
+    w.dev_status = ctx->status;
+    // segment table: int32 offsets, eps, minPts (host arrays are read before
+    // this call returns: the copies are from pageable memory)
+    std::vector<int> off32((size_t)nseg + 1);
+    for (int32_t k = 0; k <= nseg; k++)
+        off32[k] = (int)offsets[k];
+    for (int32_t k = 0; k < nseg; k++) {
+        w.any_fof |= minpts[k] <= 2;
+        w.any_dbscan |= minpts[k] > 2;
+    }
+    cudaMemcpyAsync(w.seg_off, off32.data(), off32.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(w.seg_eps_in, eps, (size_t)nseg * sizeof(float), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(w.seg_minpts_in, minpts, (size_t)nseg * sizeof(int), cudaMemcpyHostToDevice, s);
+    int seg_bits = 0;
+    while ((1ll << seg_bits) < (long long)nseg)
+        seg_bits++;
+    Params p;
+    resolve_params(nullptr, p);
+    prof_begin(s);
+    stage_segments_batch(w, w.seg_eps_in, w.seg_minpts_in, seg_bits, s);
+    run_stages(w, points, labels, p, s);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(ws, s);
+    return cuda_status(e);
 }
 
 }  // extern "C"

@@ -102,10 +102,12 @@ abx_status abx_bvh_build(const float *points, int64_t n, int32_t leaf_size, abx_
     h->w.n_sms = n_sms;
     h->w.dev_status = status;
     Params p{leaf_size ? leaf_size : 4, 0, 0, 256};
-    stage_bounds_quant(h->w, points, 0.0f, p, s);
+    h->w.any_fof = true;
+    stage_segments_single(h->w, 0.0f, 2, s);
+    stage_bounds_quant(h->w, points, p, s);
     stage_morton_sort(h->w, points, s);
-    stage_gather(h->w, points, 2, s);
-    stage_cells_leaves(h->w, 0.0f, 2, p, s);
+    stage_gather(h->w, points, s);
+    stage_cells_leaves(h->w, p, s);
     stage_hierarchy(h->w, s);
     if (cudaGetLastError() != cudaSuccess) {
         cudaFreeAsync(h->ws, s);

@@ -27,23 +27,61 @@ constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr unsigned DENSE_BIT = 0x80000000u;
 
+// Per-segment device state: one entry per independent point set of a call
+// (a single clustering call has one segment; a batch has many).
+struct SegState {
+    int lo_enc[3], hi_enc[3];   // ordered-int encoded bounds
+    float lo[3];                // segment minimum (its grid origin)
+    float inv_step;             // Morton quantisation scale
+    float e2;                   // fl(eps * eps)
+    int minpts;
+    int bits;                   // Morton bits per axis used by this segment
+    int dense_ok;               // dense cells usable (cell grid = Morton prefix)
+    int root;                   // root of the segment's subtree
+    int pad;
+};
+
 // Per-call device state (lives in the call's workspace).
 struct State {
-    int lo_enc[3], hi_enc[3];   // ordered-int encoded bounds
-    float lo[3];                // scene minimum (grid origin)
-    float inv_step;             // Morton quantisation scale
-    int bits;                   // Morton bits per axis (<= 21)
+    int nseg;                   // independent point sets in this call
+    int seg_bits;               // bits of the segment id at the top of a key
+    int max_bits;               // widest per-axis Morton width over segments
+    int shift;                  // key = segment << shift | Morton code
     int sub;                    // Morton bits per axis below the dense-cell side
-    int dense_ok;               // dense cells usable (cell grid = Morton prefix)
-    int n_passes;               // active radix passes
+    int dense_ok;               // some segment uses dense cells
+    int n_passes;               // candidate radix passes
+    int n_active;               // radix passes run (the rest are constant digits)
     int pass_ord[MAX_PASSES];   // order of pass p among the active ones, -1 = skipped
     unsigned tile_ctr[MAX_PASSES + 4];
     unsigned hist[MAX_PASSES][RADIX];   // digit histograms, then exclusive offsets
-    int n_cells;
+    int n_cells;                // dense cells found
     int n_leaves;
-    int root;
-    int pad[5];
+    int root;                   // root of the whole hierarchy
+    int frontier_count;         // nodes finishing the build in its global phase
+    int bits;                   // Morton bits per axis of segment 0 (diagnostics)
+    int pad[3];
 };
+
+// Segment of input index i: the largest s with off[s] <= i (empty segments
+// are skipped because their successor has the same offset).
+__device__ __forceinline__ int seg_of_input(const int *__restrict__ off, int nseg, int64_t i)
+{
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int64_t)__ldg(off + mid) <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Segment of a sorted point, read from the top bits of its key.
+__device__ __forceinline__ int seg_of_key(unsigned long long key, int shift)
+{
+    return shift >= 64 ? 0 : (int)(key >> shift);
+}
 
 // ---- FP32 exact predicate ---------------------------------------------------
 // d2 = fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)), every operation rounded to

@@ -48,7 +48,7 @@ static abx_status noalloc_setup(NoAllocDevice **out)
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     NoAllocDevice &d = g_noalloc_dev[dev];
     if (!d.ready) {
-        if (work_bytes(NOALLOC_MAX_POINTS) > NOALLOC_BYTES)
+        if (work_bytes(NOALLOC_MAX_POINTS, 1) > NOALLOC_BYTES)
             return ABX_EINTERNAL;
         if (cudaGetSymbolAddress(&d.ws, g_noalloc_ws) != cudaSuccess || !d.ws)
             return ABX_ECUDA;
@@ -85,16 +85,18 @@ extern "C" abx_status abx_dbscan_noalloc(const float *points, int64_t n, float e
         return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Work w;
-    work_carve(w, d->ws, n);
+    work_carve(w, d->ws, n, 1);
     w.n_sms = d->n_sms;
     w.dev_status = d->status;
-    w.stats = nullptr;
+    w.any_fof = minpts <= 2;
+    w.any_dbscan = !w.any_fof;
     const Params p{4, 1, 0, 256};
-    stage_bounds_quant(w, points, eps, p, s);
+    stage_segments_single(w, eps, minpts, s);
+    stage_bounds_quant(w, points, p, s);
     stage_morton_sort(w, points, s);
-    stage_gather(w, points, minpts, s);
-    stage_cells_leaves(w, eps, minpts, p, s);
+    stage_gather(w, points, s);
+    stage_cells_leaves(w, p, s);
     stage_hierarchy(w, s);
-    stage_cluster(w, eps, minpts, p, labels, s);
+    stage_cluster(w, p, labels, s);
     return cudaGetLastError() == cudaSuccess ? ABX_OK : ABX_ECUDA;
 }

@@ -52,20 +52,14 @@ struct TravStats {
 };
 
 template <bool FOF, bool STATS>
-__global__ void k_union(int64_t n, const State *__restrict__ st, const float4 *__restrict__ spts,
-                        const float4 *__restrict__ nodes, const int *__restrict__ leaf_of,
-                        const int *__restrict__ leaf_first, int *parent, unsigned char *core, float e2,
-                        unsigned *dev_status, TravStats *stats)
+__device__ __forceinline__ void union_query(const int i, const float e2, const Tree &T,
+                                            const float4 *__restrict__ spts, const int *__restrict__ leaf_of,
+                                            int *parent, unsigned char *core, unsigned *dev_status,
+                                            TravStats *stats)
 {
-    const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i64 >= n)
-        return;
-    const int i = (int)i64;
-    if (!FOF && !core[i])
-        return;
-    const Tree T{nodes, leaf_first, st->n_leaves};
     const int L = T.L;
     const float4 p = spts[i];
+    const int *__restrict__ leaf_first = T.leaf_first;
     bool found = false;
     unsigned c_visit = 0, c_leaf = 0, c_test = 0, c_union = 0;
 
@@ -155,12 +149,50 @@ __global__ void k_union(int64_t n, const State *__restrict__ st, const float4 *_
     }
 }
 
+template <bool FOF, bool STATS>
+__global__ void k_union(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
+                        const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                        const int *__restrict__ leaf_of, const int *__restrict__ leaf_first, int *parent,
+                        unsigned char *core, unsigned *dev_status, TravStats *stats)
+{
+    const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i64 >= n)
+        return;
+    const int i = (int)i64;
+    if (!FOF && !core[i])
+        return;
+    const Tree T{nodes, leaf_first, st->n_leaves};
+    union_query<FOF, STATS>(i, seg[0].e2, T, spts, leaf_of, parent, core, dev_status, stats);
+}
+
+// Many segments: each query takes its segment's eps and mode from its key.
+template <bool STATS>
+__global__ void k_union_seg(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
+                            const unsigned long long *k0, const unsigned long long *k1,
+                            const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                            const int *__restrict__ leaf_of, const int *__restrict__ leaf_first, int *parent,
+                            unsigned char *core, unsigned *dev_status, TravStats *stats)
+{
+    const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i64 >= n)
+        return;
+    const int i = (int)i64;
+    const unsigned long long *keys = (st->n_active & 1) ? k1 : k0;
+    const SegState &g = seg[seg_of_key(keys[i], st->shift)];
+    const Tree T{nodes, leaf_first, st->n_leaves};
+    if (g.minpts <= 2)
+        union_query<true, STATS>(i, g.e2, T, spts, leaf_of, parent, core, dev_status, stats);
+    else if (core[i])
+        union_query<false, STATS>(i, g.e2, T, spts, leaf_of, parent, core, dev_status, stats);
+}
+
 // ---- core counting with early termination (minPts > 2) -------------------------------
 
-__global__ void k_count(int64_t n, const State *__restrict__ st,
-                                               const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
-                                               const int *__restrict__ leaf_first, unsigned char *core, float e2,
-                                               int minpts, unsigned *dev_status)
+template <bool SEG>
+__global__ void k_count(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
+                        const unsigned long long *k0, const unsigned long long *k1,
+                        const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                        const int *__restrict__ leaf_first, unsigned char *core, unsigned *dev_status)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i64 >= n)
@@ -168,11 +200,21 @@ __global__ void k_count(int64_t n, const State *__restrict__ st,
     const int i = (int)i64;
     if (core[i])
         return;  // member of a dense cell
+    int s = 0;
+    if (SEG) {
+        const unsigned long long *keys = (st->n_active & 1) ? k1 : k0;
+        s = seg_of_key(keys[i], st->shift);
+    }
+    const SegState &g = seg[s];
+    const int minpts = g.minpts;
+    if (SEG && minpts <= 2)
+        return;  // a friends-of-friends segment needs no counting
+    const float e2 = g.e2;
     const Tree T{nodes, leaf_first, st->n_leaves};
     const int L = T.L;
     const float4 p = spts[i];
     int cnt = 0;
-    int node = st->root;
+    int node = g.root;
     unsigned steps = 0;
     while (node != SENTINEL) {
         if (!node_ok(node, L, steps, dev_status))
@@ -183,9 +225,9 @@ __global__ void k_count(int64_t n, const State *__restrict__ st,
                 node = __float_as_int(lo.w);
                 continue;
             }
-            const int s = (int)(__float_as_uint(lo.w) & ~DENSE_BIT);
+            const int s0 = (int)(__float_as_uint(lo.w) & ~DENSE_BIT);
             const int e = leaf_first[node - (L - 1) + 1];
-            for (int j = s; j < e; j++) {
+            for (int j = s0; j < e; j++) {
                 float4 q = __ldg(spts + j);
                 if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2 && ++cnt >= minpts) {
                     core[i] = 1;
@@ -203,11 +245,12 @@ __global__ void k_count(int64_t n, const State *__restrict__ st,
 // (b is never in a union, so nothing else reads or writes that word) and the
 // cluster's smallest border index is kept in bmin[root].
 
-__global__ void k_border(int64_t n, const State *__restrict__ st,
-                                                const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
-                                                const int *__restrict__ leaf_first, int *parent,
-                                                const unsigned char *__restrict__ core, int *bmin, float e2,
-                                                unsigned *dev_status)
+template <bool SEG>
+__global__ void k_border(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
+                         const unsigned long long *k0, const unsigned long long *k1,
+                         const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                         const int *__restrict__ leaf_first, int *parent, const unsigned char *__restrict__ core,
+                         int *bmin, unsigned *dev_status)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i64 >= n)
@@ -215,11 +258,20 @@ __global__ void k_border(int64_t n, const State *__restrict__ st,
     const int i = (int)i64;
     if (core[i])
         return;
+    int s = 0;
+    if (SEG) {
+        const unsigned long long *keys = (st->n_active & 1) ? k1 : k0;
+        s = seg_of_key(keys[i], st->shift);
+    }
+    const SegState &g = seg[s];
+    if (SEG && g.minpts <= 2)
+        return;  // friends-of-friends: no border points
+    const float e2 = g.e2;
     const Tree T{nodes, leaf_first, st->n_leaves};
     const int L = T.L;
     const float4 p = spts[i];
     int best_k = 0x7fffffff, best_r = -1;
-    int node = st->root;
+    int node = g.root;
     unsigned steps = 0;
     while (node != SENTINEL) {
         if (!node_ok(node, L, steps, dev_status))
@@ -231,9 +283,9 @@ __global__ void k_border(int64_t n, const State *__restrict__ st,
                 continue;
             }
             const unsigned lw = __float_as_uint(lo.w);
-            const int s = (int)(lw & ~DENSE_BIT);
+            const int s0 = (int)(lw & ~DENSE_BIT);
             const int e = leaf_first[node - (L - 1) + 1];
-            for (int j = s; j < e; j++) {
+            for (int j = s0; j < e; j++) {
                 if (!core[j])
                     continue;
                 float4 q = __ldg(spts + j);
@@ -259,10 +311,14 @@ __global__ void k_border(int64_t n, const State *__restrict__ st,
 
 // ---- labels -----------------------------------------------------------------------------------
 // Cluster id = the smallest original index among the members: the root's
-// (smallest core index) or a smaller border index.  Scattered to input order.
+// (smallest core index) or a smaller border index; scattered to input order,
+// relative to the segment's first point.
 
-template <bool FOF>
-__global__ void __launch_bounds__(256) k_finalize(int64_t n, const float4 *__restrict__ spts, int *parent,
+template <bool SEG>
+__global__ void __launch_bounds__(256) k_finalize(int64_t n, const State *__restrict__ st,
+                                                  const SegState *__restrict__ seg, const int *__restrict__ off,
+                                                  const unsigned long long *k0, const unsigned long long *k1,
+                                                  const float4 *__restrict__ spts, int *parent,
                                                   const unsigned char *__restrict__ core,
                                                   const int *__restrict__ bmin, int32_t *labels)
 {
@@ -270,13 +326,19 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t n, const float4 *__res
     if (i64 >= n)
         return;
     const int i = (int)i64;
+    int s = 0;
+    if (SEG) {
+        const unsigned long long *keys = (st->n_active & 1) ? k1 : k0;
+        s = seg_of_key(keys[i], st->shift);
+    }
+    const bool fof = seg[s].minpts <= 2;
     int lab = -1;
     if (core[i]) {
         int r = uf_find(parent, i);
         lab = orig_of(spts, r);
-        if (!FOF)
+        if (!fof)
             lab = min(lab, bmin[r]);
-    } else if (!FOF) {
+    } else if (!fof) {
         int r = parent[i];
         if (r != i)
             lab = min(orig_of(spts, r), bmin[r]);
@@ -284,47 +346,71 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t n, const float4 *__res
     // labels were preset to -1: only cluster members are scattered
     const int o = __float_as_int(spts[i].w);
     if (lab >= 0 && (unsigned)o < (unsigned)n)
-        labels[o] = lab;
+        labels[o] = SEG ? lab - off[s] : lab;
 }
 
-void stage_cluster(const Work &w, float eps, int minpts, const Params &p, int32_t *labels, cudaStream_t s)
+void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t s)
 {
-    const float e2 = eps * eps;
-    cudaMemsetAsync(labels, 0xff, (size_t)w.n * sizeof(int32_t), s);  // noise = -1
     const int B = p.block;
     const int g = div_up(w.n, B);
-    if (minpts <= 2) {
-        if (w.stats)
-            k_union<true, true><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent,
-                                                w.core, e2, w.dev_status, (TravStats *)w.stats);
-        else
-            k_union<true, false><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent,
-                                                 w.core, e2, w.dev_status, nullptr);
-        note_launch();
-        prof_mark(ST_UNION, s);
-        k_finalize<true><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.spts, w.parent, w.core, w.bmin, labels);
-        note_launch();
-        prof_mark(ST_FINALIZE, s);
+    TravStats *stats = (TravStats *)w.stats;
+    cudaMemsetAsync(labels, 0xff, (size_t)w.n * sizeof(int32_t), s);  // noise = -1
+    if (w.nseg == 1) {
+        if (w.any_fof) {
+            if (stats)
+                k_union<true, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
+                                                    w.parent, w.core, w.dev_status, stats);
+            else
+                k_union<true, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
+                                                     w.parent, w.core, w.dev_status, nullptr);
+            note_launch();
+            prof_mark(ST_UNION, s);
+        } else {
+            k_count<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
+                                           w.core, w.dev_status);
+            note_launch();
+            prof_mark(ST_COUNT, s);
+            if (stats)
+                k_union<false, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
+                                                     w.parent, w.core, w.dev_status, stats);
+            else
+                k_union<false, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
+                                                      w.parent, w.core, w.dev_status, nullptr);
+            note_launch();
+            prof_mark(ST_UNION, s);
+            k_border<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
+                                            w.parent, w.core, w.bmin, w.dev_status);
+            note_launch();
+            prof_mark(ST_BORDER, s);
+        }
+        k_finalize<false><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.st, w.seg, w.seg_off, w.keys[0], w.keys[1],
+                                                           w.spts, w.parent, w.core, w.bmin, labels);
     } else {
-        k_count<<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_first, w.core, e2, minpts, w.dev_status);
-        note_launch();
-        prof_mark(ST_COUNT, s);
-        if (w.stats)
-            k_union<false, true><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent,
-                                                 w.core, e2, w.dev_status, (TravStats *)w.stats);
+        if (w.any_dbscan) {
+            k_count<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
+                                          w.core, w.dev_status);
+            note_launch();
+            prof_mark(ST_COUNT, s);
+        }
+        if (stats)
+            k_union_seg<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_of,
+                                              w.leaf_first, w.parent, w.core, w.dev_status, stats);
         else
-            k_union<false, false><<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, w.parent,
-                                                  w.core, e2, w.dev_status, nullptr);
+            k_union_seg<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_of,
+                                               w.leaf_first, w.parent, w.core, w.dev_status, nullptr);
         note_launch();
         prof_mark(ST_UNION, s);
-        k_border<<<g, B, 0, s>>>(w.n, w.st, w.spts, w.nodes, w.leaf_first, w.parent, w.core, w.bmin, e2,
-                                 w.dev_status);
-        note_launch();
-        prof_mark(ST_BORDER, s);
-        k_finalize<false><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.spts, w.parent, w.core, w.bmin, labels);
-        note_launch();
-        prof_mark(ST_FINALIZE, s);
+        if (w.any_dbscan) {
+            k_border<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
+                                           w.parent, w.core, w.bmin, w.dev_status);
+            note_launch();
+            prof_mark(ST_BORDER, s);
+        }
+        k_finalize<true><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.st, w.seg, w.seg_off, w.keys[0], w.keys[1],
+                                                          w.spts, w.parent, w.core, w.bmin, labels);
     }
+    note_launch();
+    prof_mark(ST_FINALIZE, s);
 }
 
 }  // namespace abx

@@ -14,13 +14,44 @@
 
 namespace abx {
 
-// ---- bounds -------------------------------------------------------------------
+// ---- segments and bounds -----------------------------------------------------------
 
-__global__ void k_init_state(State *st)
+__device__ __forceinline__ void seg_reset(SegState &g, float eps, int minpts)
 {
-    if (threadIdx.x < 3) {
-        st->lo_enc[threadIdx.x] = float_to_ordered(__int_as_float(0x7f800000));   // +inf
-        st->hi_enc[threadIdx.x] = float_to_ordered(__int_as_float((int)0xff800000));  // -inf
+    for (int k = 0; k < 3; k++) {
+        g.lo_enc[k] = float_to_ordered(__int_as_float(0x7f800000));          // +inf
+        g.hi_enc[k] = float_to_ordered(__int_as_float((int)0xff800000));     // -inf
+        g.lo[k] = 0.0f;
+    }
+    g.inv_step = 0.0f;
+    g.e2 = __fmul_rn(eps, eps);
+    g.minpts = minpts;
+    g.bits = 0;
+    g.dense_ok = 0;
+    g.root = SENTINEL;
+    g.pad = 0;
+}
+
+// A single clustering call: one segment covering all n points.
+__global__ void k_init_single(State *st, SegState *seg, int *off, int64_t n, float eps, int minpts)
+{
+    if (threadIdx.x == 0) {
+        seg_reset(seg[0], eps, minpts);
+        off[0] = 0;
+        off[1] = (int)n;
+        st->nseg = 1;
+        st->seg_bits = 0;
+    }
+}
+
+// A batch: segment k gets eps[k], minpts[k] (device copies of the host arrays).
+__global__ void k_init_batch(State *st, SegState *seg, int nseg, const float *eps, const int *minpts, int seg_bits)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x)
+        seg_reset(seg[k], eps[k], minpts[k]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->nseg = nseg;
+        st->seg_bits = seg_bits;
     }
 }
 
@@ -40,10 +71,32 @@ struct MinMax {
         else if (axis == 1) { mn1 = fminf(mn1, v); mx1 = fmaxf(mx1, v); }
         else { mn2 = fminf(mn2, v); mx2 = fmaxf(mx2, v); }
     }
+    __device__ __forceinline__ void warp_reduce()
+    {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn0 = fminf(mn0, __shfl_xor_sync(~0u, mn0, o));
+            mn1 = fminf(mn1, __shfl_xor_sync(~0u, mn1, o));
+            mn2 = fminf(mn2, __shfl_xor_sync(~0u, mn2, o));
+            mx0 = fmaxf(mx0, __shfl_xor_sync(~0u, mx0, o));
+            mx1 = fmaxf(mx1, __shfl_xor_sync(~0u, mx1, o));
+            mx2 = fmaxf(mx2, __shfl_xor_sync(~0u, mx2, o));
+        }
+    }
+    __device__ __forceinline__ void publish(SegState &g) const
+    {
+        atomicMin(&g.lo_enc[0], float_to_ordered(mn0));
+        atomicMin(&g.lo_enc[1], float_to_ordered(mn1));
+        atomicMin(&g.lo_enc[2], float_to_ordered(mn2));
+        atomicMax(&g.hi_enc[0], float_to_ordered(mx0));
+        atomicMax(&g.hi_enc[1], float_to_ordered(mx1));
+        atomicMax(&g.hi_enc[2], float_to_ordered(mx2));
+    }
 };
 
+// One segment: float4 loads over the flat coordinate array, block reduction,
+// one atomic per value per block.
 __global__ void __launch_bounds__(256) k_bounds(const float *__restrict__ pts, int64_t n, int aligned,
-                                                State *st, unsigned *dev_status)
+                                                SegState *seg, unsigned *dev_status)
 {
     MinMax m;
     m.init();
@@ -66,15 +119,7 @@ __global__ void __launch_bounds__(256) k_bounds(const float *__restrict__ pts, i
     for (int64_t e = done + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride)
         m.upd((int)(e % 3), __ldg(pts + e));
 
-    // block reduction
-    for (int o = 16; o > 0; o >>= 1) {
-        m.mn0 = fminf(m.mn0, __shfl_xor_sync(~0u, m.mn0, o));
-        m.mn1 = fminf(m.mn1, __shfl_xor_sync(~0u, m.mn1, o));
-        m.mn2 = fminf(m.mn2, __shfl_xor_sync(~0u, m.mn2, o));
-        m.mx0 = fmaxf(m.mx0, __shfl_xor_sync(~0u, m.mx0, o));
-        m.mx1 = fmaxf(m.mx1, __shfl_xor_sync(~0u, m.mx1, o));
-        m.mx2 = fmaxf(m.mx2, __shfl_xor_sync(~0u, m.mx2, o));
-    }
+    m.warp_reduce();
     unsigned anybad = __any_sync(~0u, m.bad);
     __shared__ float sm[8][6];
     __shared__ int sbad;
@@ -95,80 +140,140 @@ __global__ void __launch_bounds__(256) k_bounds(const float *__restrict__ pts, i
         for (int i = 1; i < (int)(blockDim.x >> 5); i++)
             v = k < 3 ? fminf(v, sm[i][k]) : fmaxf(v, sm[i][k]);
         if (k < 3)
-            atomicMin(&st->lo_enc[k], float_to_ordered(v));
+            atomicMin(&seg[0].lo_enc[k], float_to_ordered(v));
         else
-            atomicMax(&st->hi_enc[k - 3], float_to_ordered(v));
+            atomicMax(&seg[0].hi_enc[k - 3], float_to_ordered(v));
     }
     if (threadIdx.x == 0 && sbad)
         atomicOr(dev_status, DEV_NONFINITE);
 }
 
-// One thread: choose the quantisation and the candidate radix passes.
-__global__ void k_quant(State *st, float eps, int dense_on, int sub_bits)
+// Many segments: one point per lane; a warp whose points share a segment
+// reduces first and publishes once, otherwise every lane publishes.
+__global__ void __launch_bounds__(256) k_bounds_seg(const float *__restrict__ pts, int64_t n, SegState *seg,
+                                                    const int *__restrict__ off, int nseg, unsigned *dev_status)
 {
-    float lo[3], ext = 0.0f;
-    for (int k = 0; k < 3; k++) {
-        lo[k] = ordered_to_float(st->lo_enc[k]);
-        float hi = ordered_to_float(st->hi_enc[k]);
-        float e = hi - lo[k];
-        if (!(e >= 0.0f) || !isfinite(lo[k]) || !isfinite(hi))
-            e = 0.0f;  // non-finite input: already flagged; any key will do
-        if (!isfinite(e))
-            e = 3.0e38f;
-        ext = fmaxf(ext, e);
-        st->lo[k] = isfinite(lo[k]) ? lo[k] : 0.0f;
-    }
-    // dense-cell side h slightly below eps/sqrt(3): cell diagonal <= eps
-    float h = eps * 0.57735026f * 0.999f;
-    int bits = 21, sub = 0, dense_ok = 0;
-    float inv_step = 0.0f;
-    if (h > 1e-30f && isfinite(h)) {
-        float ratio = ext / h;
-        if (ratio < (float)((1 << (21 - sub_bits)) - 2)) {
-            int bc = 1;
-            while ((float)(1 << bc) < ratio + 1.0f)
-                bc++;
-            sub = sub_bits;
-            bits = bc + sub;
-            inv_step = (float)(1 << sub) / h;
-            dense_ok = dense_on;
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += wstride) {
+        const int64_t i = base + lane;
+        const bool valid = i < n;
+        MinMax m;
+        m.init();
+        int s = -1;
+        if (valid) {
+            s = seg_of_input(off, nseg, i);
+            m.upd(0, __ldg(pts + 3 * i));
+            m.upd(1, __ldg(pts + 3 * i + 1));
+            m.upd(2, __ldg(pts + 3 * i + 2));
+            bad |= m.bad;
+        }
+        const int s0 = __shfl_sync(~0u, s, 0);
+        if (__all_sync(~0u, s == s0 || !valid) && s0 >= 0) {
+            m.warp_reduce();
+            if (lane == 0)
+                m.publish(seg[s0]);
+        } else if (valid) {
+            m.publish(seg[s]);
         }
     }
-    if (inv_step == 0.0f) {
-        bits = 21;
-        sub = 0;
-        float is = ext > 0.0f ? (float)((1 << 21) - 1) / ext : 0.0f;
-        inv_step = isfinite(is) ? is : 0.0f;
+    if (__any_sync(~0u, bad) && lane == 0)
+        atomicOr(dev_status, DEV_NONFINITE);
+}
+
+// One thread per segment: choose the quantisation.  The step is the dense-cell
+// side h (slightly below eps/sqrt(3), so a cell's diagonal is at most eps)
+// divided by 2^sub, as long as the extent spans few enough cells for the
+// per-axis width cap; otherwise extent / (2^cap - 1) and no dense cells.
+__global__ void k_quant(State *st, SegState *seg, int nseg, int dense_on, int sub_bits)
+{
+    const int cap = min(21, (64 - st->seg_bits) / 3);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        st->sub = sub_bits;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x) {
+        SegState &g = seg[k];
+        float lo[3], ext = 0.0f;
+        for (int a = 0; a < 3; a++) {
+            lo[a] = ordered_to_float(g.lo_enc[a]);
+            float hi = ordered_to_float(g.hi_enc[a]);
+            float e = hi - lo[a];
+            if (!(e >= 0.0f) || !isfinite(lo[a]) || !isfinite(hi))
+                e = 0.0f;  // empty segment or non-finite input (flagged): any key will do
+            if (!isfinite(e))
+                e = 3.0e38f;
+            ext = fmaxf(ext, e);
+            g.lo[a] = isfinite(lo[a]) ? lo[a] : 0.0f;
+        }
+        const float eps = sqrtf(g.e2);
+        const float h = eps * 0.57735026f * 0.999f;
+        int bits = cap, dense_ok = 0;
+        float inv_step = 0.0f;
+        if (h > 1e-30f && isfinite(h) && sub_bits < cap) {
+            const float ratio = ext / h;
+            if (ratio < (float)((1 << (cap - sub_bits)) - 2)) {
+                int bc = 1;
+                while ((float)(1 << bc) < ratio + 1.0f)
+                    bc++;
+                bits = bc + sub_bits;
+                inv_step = (float)(1 << sub_bits) / h;
+                dense_ok = dense_on;
+            }
+        }
+        if (inv_step == 0.0f) {
+            bits = cap;
+            float is = ext > 0.0f ? (float)((1 << cap) - 1) / ext : 0.0f;
+            inv_step = isfinite(is) ? is : 0.0f;
+        }
+        g.inv_step = inv_step;
+        g.bits = bits;
+        g.dense_ok = dense_ok;
+        atomicMax(&st->max_bits, bits);
+        if (dense_ok)
+            atomicOr(&st->dense_ok, 1);
+        if (k == 0)
+            st->bits = bits;
     }
-    st->inv_step = inv_step;
-    st->bits = bits;
-    st->sub = sub;
-    st->dense_ok = dense_ok;
-    int np = (3 * bits + RADIX_BITS - 1) / RADIX_BITS;
-    st->n_passes = np;
 }
 
 // ---- Morton keys + the upfront digit histograms ---------------------------------
+// key = segment << shift | Morton code (shift = 3 * the widest per-axis width),
+// so segments sort apart and each forms its own subtree.
 
+template <bool SEG>
 __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ pts, int64_t n, State *st,
+                                                const SegState *__restrict__ seg, const int *__restrict__ off,
                                                 unsigned long long *__restrict__ keys)
 {
     __shared__ unsigned sh[MAX_PASSES * RADIX];
     for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x)
         sh[i] = 0;
-    const float lx = st->lo[0], ly = st->lo[1], lz = st->lo[2];
-    const float is = st->inv_step;
-    const int np = st->n_passes;
-    const float qmax = (float)((1u << st->bits) - 1u);
+    const int nseg = st->nseg;
+    const int shift = 3 * st->max_bits;
+    const int np = (st->seg_bits + shift + RADIX_BITS - 1) / RADIX_BITS;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->shift = shift;
+        st->n_passes = np;
+    }
+    float lx = seg[0].lo[0], ly = seg[0].lo[1], lz = seg[0].lo[2], is = seg[0].inv_step;
+    float qmax = (float)((1u << seg[0].bits) - 1u);
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long top = 0;
+        if (SEG) {
+            const int s = seg_of_input(off, nseg, i);
+            const SegState &g = seg[s];
+            lx = g.lo[0]; ly = g.lo[1]; lz = g.lo[2]; is = g.inv_step;
+            qmax = (float)((1u << g.bits) - 1u);
+            top = (unsigned long long)s << shift;
+        }
         float x = __ldg(pts + 3 * i), y = __ldg(pts + 3 * i + 1), z = __ldg(pts + 3 * i + 2);
         float tx = (x - lx) * is, ty = (y - ly) * is, tz = (z - lz) * is;
         unsigned qx = tx < qmax ? (unsigned)fmaxf(tx, 0.0f) : (unsigned)qmax;
         unsigned qy = ty < qmax ? (unsigned)fmaxf(ty, 0.0f) : (unsigned)qmax;
         unsigned qz = tz < qmax ? (unsigned)fmaxf(tz, 0.0f) : (unsigned)qmax;
-        unsigned long long key = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+        unsigned long long key = top | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
         keys[i] = key;
         for (int p = 0; p < np; p++)
             atomicAdd(&sh[p * RADIX + (unsigned)((key >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
@@ -206,7 +311,7 @@ __global__ void k_sort_plan(State *st, int64_t n)
         int ord = 0;
         for (int p = 0; p < MAX_PASSES; p++)
             st->pass_ord[p] = active[p] ? ord++ : -1;
-        st->pad[0] = ord;  // number of active passes
+        st->n_active = ord;
     }
 }
 
@@ -389,16 +494,21 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, unsigned
 
 // ---- gather -----------------------------------------------------------------------
 // spts[k] = (x, y, z, original index) of the k-th point in key order; resets
-// the union-find and the core flags.
+// the union-find, the core flags (all core when the segment's minPts is 1)
+// and the border minima.
 
+template <bool SEG>
 __global__ void __launch_bounds__(256) k_gather(const float *__restrict__ pts, int64_t n, const State *st,
-                                                const unsigned *v0, const unsigned *v1, float4 *spts,
-                                                int *parent, unsigned char *core, int *bmin, int minpts,
+                                                const SegState *__restrict__ seg, const unsigned long long *k0,
+                                                const unsigned long long *k1, const unsigned *v0, const unsigned *v1,
+                                                float4 *spts, int *parent, unsigned char *core, int *bmin,
                                                 unsigned *dev_status)
 {
-    const int na = st->pad[0];
+    const int na = st->n_active;
     const unsigned *perm = na == 0 ? nullptr : ((na & 1) ? v1 : v0);
-    const unsigned char c0 = minpts <= 1 ? 1 : 0;
+    const unsigned long long *keys = (na & 1) ? k1 : k0;
+    const int shift = st->shift;
+    unsigned char c0 = seg[0].minpts <= 1 ? 1 : 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         unsigned o = perm ? perm[k] : (unsigned)k;
         if ((int64_t)o >= n) {  // never for a correct sort
@@ -408,6 +518,8 @@ __global__ void __launch_bounds__(256) k_gather(const float *__restrict__ pts, i
         float x = __ldg(pts + 3 * (int64_t)o), y = __ldg(pts + 3 * (int64_t)o + 1), z = __ldg(pts + 3 * (int64_t)o + 2);
         spts[k] = make_float4(x, y, z, __int_as_float((int)o));
         parent[k] = (int)k;
+        if (SEG)
+            c0 = seg[seg_of_key(keys[k], shift)].minpts <= 1 ? 1 : 0;
         core[k] = c0;
         if (bmin)
             bmin[k] = 0x7fffffff;
@@ -425,20 +537,39 @@ static int grid_for(const Work &w, int64_t n, int block, int per_sm = 8)
     return (int)(g < 1 ? 1 : g);
 }
 
-void stage_bounds_quant(const Work &w, const float *points, float eps, const Params &p, cudaStream_t s)
+void stage_segments_single(const Work &w, float eps, int minpts, cudaStream_t s)
 {
     cudaMemsetAsync(w.st, 0, sizeof(State), s);
-    k_init_state<<<1, 32, 0, s>>>(w.st);
-    int aligned = (reinterpret_cast<uintptr_t>(points) & 15) == 0;
-    k_bounds<<<grid_for(w, (3 * w.n + 3) / 4, 256), 256, 0, s>>>(points, w.n, aligned, w.st, w.dev_status);
-    k_quant<<<1, 1, 0, s>>>(w.st, eps, p.dense, p.sub_bits);
-    note_launch(3);
+    k_init_single<<<1, 32, 0, s>>>(w.st, w.seg, w.seg_off, w.n, eps, minpts);
+    note_launch();
+}
+
+void stage_segments_batch(const Work &w, const float *eps_dev, const int *minpts_dev, int seg_bits, cudaStream_t s)
+{
+    cudaMemsetAsync(w.st, 0, sizeof(State), s);
+    k_init_batch<<<div_up(w.nseg, 128), 128, 0, s>>>(w.st, w.seg, w.nseg, eps_dev, minpts_dev, seg_bits);
+    note_launch();
+}
+
+void stage_bounds_quant(const Work &w, const float *points, const Params &p, cudaStream_t s)
+{
+    if (w.nseg == 1) {
+        int aligned = (reinterpret_cast<uintptr_t>(points) & 15) == 0;
+        k_bounds<<<grid_for(w, (3 * w.n + 3) / 4, 256), 256, 0, s>>>(points, w.n, aligned, w.seg, w.dev_status);
+    } else {
+        k_bounds_seg<<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.seg, w.seg_off, w.nseg, w.dev_status);
+    }
+    k_quant<<<div_up(w.nseg, 128), 128, 0, s>>>(w.st, w.seg, w.nseg, p.dense, p.sub_bits);
+    note_launch(2);
     prof_mark(ST_BOUNDS, s);
 }
 
 void stage_morton_sort(const Work &w, const float *points, cudaStream_t s)
 {
-    k_morton<<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.keys[0]);
+    if (w.nseg == 1)
+        k_morton<false><<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0]);
+    else
+        k_morton<true><<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0]);
     note_launch();
     prof_mark(ST_MORTON, s);
     k_sort_plan<<<1, RADIX, 0, s>>>(w.st, w.n);
@@ -452,10 +583,17 @@ void stage_morton_sort(const Work &w, const float *points, cudaStream_t s)
     prof_mark(ST_SORT, s);
 }
 
-void stage_gather(const Work &w, const float *points, int minpts, cudaStream_t s)
+void stage_gather(const Work &w, const float *points, cudaStream_t s)
 {
-    k_gather<<<grid_for(w, w.n, 256, 16), 256, 0, s>>>(points, w.n, w.st, w.vals[0], w.vals[1], w.spts, w.parent,
-                                                        w.core, minpts > 2 ? w.bmin : nullptr, minpts, w.dev_status);
+    int *bmin = w.any_dbscan ? w.bmin : nullptr;
+    if (w.nseg == 1)
+        k_gather<false><<<grid_for(w, w.n, 256, 16), 256, 0, s>>>(points, w.n, w.st, w.seg, w.keys[0], w.keys[1],
+                                                                  w.vals[0], w.vals[1], w.spts, w.parent, w.core,
+                                                                  bmin, w.dev_status);
+    else
+        k_gather<true><<<grid_for(w, w.n, 256, 16), 256, 0, s>>>(points, w.n, w.st, w.seg, w.keys[0], w.keys[1],
+                                                                 w.vals[0], w.vals[1], w.spts, w.parent, w.core,
+                                                                 bmin, w.dev_status);
     note_launch();
     prof_mark(ST_GATHER, s);
 }

@@ -24,7 +24,7 @@
 
 namespace abx {
 
-__device__ __forceinline__ int final_pass_count(const State *st) { return st->pad[0]; }
+__device__ __forceinline__ int final_pass_count(const State *st) { return st->n_active; }
 
 __device__ __forceinline__ const unsigned long long *sorted_keys(const State *st, unsigned long long *const k0,
                                                                   unsigned long long *const k1)
@@ -159,6 +159,7 @@ struct LeafFlag {
     int *parent;
     unsigned char *core;
     const State *st;
+    const unsigned long long *k0, *k1;
     int leaf_size;
     int64_t n;
     __device__ bool operator()(int64_t k64) const
@@ -178,6 +179,12 @@ struct LeafFlag {
         }
         if (k == 0)
             return true;
+        if (st->nseg > 1) {  // leaves never cross segments
+            const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
+                                                         const_cast<unsigned long long *>(k1));
+            if (seg_of_key(keys[k], st->shift) != seg_of_key(keys[k - 1], st->shift))
+                return true;
+        }
         const int x = k - 1, B = leaf_size, last = (int)n - 1;
         const int d = pdelta[x];
         int yr = x + 1;  // nearest boundary on the right with level >= d
@@ -206,20 +213,25 @@ struct LeafFlag {
 // the rounded predicate is dense: every member gets the member with the
 // smallest original index as dense_root (else dense_root stays -1).
 
-__global__ void __launch_bounds__(256) k_dense_cells(int64_t n, State *st, const unsigned long long *k0,
-                                                     const unsigned long long *k1,
-                                                     const float4 *__restrict__ spts, int *dense_root, float e2,
-                                                     int min_count)
+__global__ void __launch_bounds__(256) k_dense_cells(int64_t n, State *st, const SegState *__restrict__ seg,
+                                                     const unsigned long long *k0, const unsigned long long *k1,
+                                                     const float4 *__restrict__ spts, int *dense_root)
 {
     if (!st->dense_ok)
         return;
     const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
                                                  const_cast<unsigned long long *>(k1));
-    const int sh = 3 * st->sub;
+    const int sh = 3 * st->sub, shift = st->shift;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long c = keys[k] >> sh;
+        const unsigned long long key = keys[k];
+        const unsigned long long c = key >> sh;
         if (k > 0 && (keys[k - 1] >> sh) == c)
             continue;  // not the first point of its cell
+        const SegState &g = seg[seg_of_key(key, shift)];
+        if (!g.dense_ok)
+            continue;
+        const float e2 = g.e2;
+        const int min_count = g.minpts < 2 ? 2 : g.minpts;
         int64_t e = k + 1;
         while (e < n && (keys[e] >> sh) == c && e - k < min_count)
             e++;
@@ -270,12 +282,18 @@ __global__ void __launch_bounds__(256) k_pdelta(int64_t n, const State *st, cons
         pdelta[k] = split_level(keys[k], keys[k + 1], (int)k);
 }
 
-__global__ void __launch_bounds__(256) k_leaves(const State *st, const unsigned char *__restrict__ pdelta,
+__global__ void __launch_bounds__(256) k_leaves(const State *st, SegState *seg, const unsigned long long *k0,
+                                                const unsigned long long *k1, const unsigned char *__restrict__ pdelta,
                                                 const float4 *__restrict__ spts, const int *leaf_first,
-                                                const int *dense_root, float4 *nodes, unsigned char *delta)
+                                                const int *dense_root, float4 *nodes, unsigned char *delta,
+                                                int *leaf_seg)
 {
     const int L = st->n_leaves;
     const int dense_ok = st->dense_ok;
+    const int nseg = st->nseg, shift = st->shift;
+    const int64_t n = leaf_first[L];
+    const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
+                                                 const_cast<unsigned long long *>(k1));
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L; t += gridDim.x * blockDim.x) {
         int s = leaf_first[t], e = leaf_first[t + 1];
         float4 p = spts[s];
@@ -293,6 +311,17 @@ __global__ void __launch_bounds__(256) k_leaves(const State *st, const unsigned 
         nodes[r + 1] = make_float4(hx, hy, hz, __int_as_float(SENTINEL));
         if (t < L - 1)
             delta[t] = pdelta[e - 1];  // the point-level split level at the leaf boundary
+        int sg = 0;
+        if (nseg > 1) {
+            sg = seg_of_key(keys[s], shift);
+            const bool first = s == 0 || seg_of_key(keys[s - 1], shift) != sg;
+            const bool last = e == n || seg_of_key(keys[e], shift) != sg;
+            if (first && last)
+                seg[sg].root = L - 1 + t;  // a segment of a single leaf
+        } else if (L == 1) {
+            seg[0].root = 0;
+        }
+        leaf_seg[t] = sg;
     }
 }
 
@@ -331,6 +360,21 @@ __device__ __forceinline__ void write_parent(float4 *nodes, int *right_of, int p
     right_of[p] = rc;
 }
 
+// A completed node that covers exactly the leaves of one segment is that
+// segment's root (the top of the subtree its full traversals start from).
+__device__ __forceinline__ void note_seg_root(SegState *seg, const int *leaf_seg, int nseg, int L, int p, int l,
+                                              int r)
+{
+    if (nseg == 1) {
+        if (l == 0 && r == L - 1)
+            seg[0].root = p;
+        return;
+    }
+    const int s = leaf_seg[l];
+    if ((l == 0 || leaf_seg[l - 1] != s) && (r == L - 1 || leaf_seg[r + 1] != s))
+        seg[s].root = p;
+}
+
 __device__ __forceinline__ void push_frontier(int4 *frontier, int *count, int node, int l, int r)
 {
     int k = atomicAdd(count, 1);
@@ -339,10 +383,12 @@ __device__ __forceinline__ void push_frontier(int4 *frontier, int *count, int no
 
 constexpr size_t BUILD_SMEM = (size_t)(BUILD_CHUNK - 1) * (2 * 6 * sizeof(float) + sizeof(unsigned long long));
 
-__global__ void __launch_bounds__(BUILD_CHUNK) k_build_local(State *st, const unsigned char *__restrict__ delta,
+__global__ void __launch_bounds__(BUILD_CHUNK) k_build_local(State *st, SegState *seg, const int *leaf_seg,
+                                                             const unsigned char *__restrict__ delta,
                                                              float4 *nodes, int *right_of, int4 *frontier,
                                                              int *frontier_count)
 {
+    const int nseg = st->nseg;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *stag = reinterpret_cast<unsigned long long *>(smem);
     float *sbox = reinterpret_cast<float *>(stag + (BUILD_CHUNK - 1));  // [slot][side][6]
@@ -390,6 +436,7 @@ __global__ void __launch_bounds__(BUILD_CHUNK) k_build_local(State *st, const un
             else
                 l = bound;
             write_parent(nodes, right_of, p, b, left ? node : sib, left ? sib : node, r);
+            note_seg_root(seg, leaf_seg, nseg, L, p, l, r);
             node = p;
             if (l == 0 && r == L - 1) {
                 st->root = p;
@@ -413,11 +460,13 @@ __global__ void __launch_bounds__(BUILD_CHUNK) k_build_local(State *st, const un
     }
 }
 
-__global__ void __launch_bounds__(256) k_build_global(State *st, const unsigned char *__restrict__ delta,
+__global__ void __launch_bounds__(256) k_build_global(State *st, SegState *seg, const int *leaf_seg,
+                                                      const unsigned char *__restrict__ delta,
                                                       float4 *nodes, unsigned long long *slot, int *right_of,
                                                       const int4 *frontier, const int *frontier_count)
 {
     const int L = st->n_leaves;
+    const int nseg = st->nseg;
     const int nf = *frontier_count;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
         const int4 it = frontier[f];
@@ -441,6 +490,7 @@ __global__ void __launch_bounds__(256) k_build_global(State *st, const unsigned 
             hi.x = fmaxf(hi.x, shi.x); hi.y = fmaxf(hi.y, shi.y); hi.z = fmaxf(hi.z, shi.z);
             const float b[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
             write_parent(nodes, right_of, p, b, left ? node : sib, left ? sib : node, r);
+            note_seg_root(seg, leaf_seg, nseg, L, p, l, r);
             node = p;
             if (l == 0 && r == L - 1) {
                 st->root = p;
@@ -452,17 +502,18 @@ __global__ void __launch_bounds__(256) k_build_global(State *st, const unsigned 
 
 // rope(node covering [.., b]) = right child of internal node b, or the sentinel
 __global__ void __launch_bounds__(256) k_ropes(const State *st, float4 *nodes, const int *right_of,
-                                               unsigned *dev_status)
+                                               const int *leaf_seg, unsigned *dev_status)
 {
     const int L = st->n_leaves;
+    const int nseg = st->nseg;
     const int total = 2 * L - 1;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         int b = i < L - 1 ? __float_as_int(nodes[2 * (size_t)i + 1].w) : i - (L - 1);
         int rope = SENTINEL;
         if ((unsigned)b >= (unsigned)L)
             atomicOr(dev_status, DEV_INTERNAL);  // node never completed: corrupted build
-        else if (b != L - 1)
-            rope = right_of[b];
+        else if (b != L - 1 && (nseg == 1 || leaf_seg[b] == leaf_seg[b + 1]))
+            rope = right_of[b];  // else: last leaf of its segment -> sentinel
         reinterpret_cast<int *>(nodes + 2 * (size_t)i + 1)[3] = rope;
     }
 }
@@ -478,24 +529,22 @@ static int grid_cap(const Work &w, int64_t n, int block, int per_sm = 8)
     return (int)(g < 1 ? 1 : g);
 }
 
-void stage_cells_leaves(const Work &w, float eps, int minpts, const Params &p, cudaStream_t s)
+void stage_cells_leaves(const Work &w, const Params &p, cudaStream_t s)
 {
     const int scan_tiles = div_up(w.n, SCAN_TILE);
-    const float e2 = eps * eps;
-    const int min_count = minpts < 2 ? 2 : minpts;
     cudaMemsetAsync(w.dense_root, 0xff, (size_t)w.n * sizeof(int), s);
-    k_dense_cells<<<grid_cap(w, w.n, 256, 16), 256, 0, s>>>(w.n, w.st, w.keys[0], w.keys[1], w.spts, w.dense_root,
-                                                            e2, min_count);
+    k_dense_cells<<<grid_cap(w, w.n, 256, 16), 256, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts,
+                                                            w.dense_root);
     note_launch(1);
     prof_mark(ST_CELLS, s);
     k_pdelta<<<grid_cap(w, w.n, 256, 16), 256, 0, s>>>(w.n, w.st, w.keys[0], w.keys[1], w.pdelta);
     cudaMemsetAsync(w.scan_lb, 0, w.scan_tiles * sizeof(unsigned long long), s);
-    LeafFlag lf{w.dense_root, w.pdelta, w.parent, w.core, w.st, p.leaf_size, w.n};
+    LeafFlag lf{w.dense_root, w.pdelta, w.parent, w.core, w.st, w.keys[0], w.keys[1], p.leaf_size, w.n};
     k_flag_scan<<<scan_tiles, SCAN_THREADS, 0, s>>>(w.n, lf, w.leaf_of, w.leaf_first, &w.st->n_leaves,
                                                     &w.st->tile_ctr[MAX_PASSES + 1], w.scan_lb, w.dev_status, w.st,
                                                     0);
-    k_leaves<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.st, w.pdelta, w.spts, w.leaf_first, w.dense_root, w.nodes,
-                                                   w.delta);
+    k_leaves<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.st, w.seg, w.keys[0], w.keys[1], w.pdelta, w.spts, w.leaf_first,
+                                                   w.dense_root, w.nodes, w.delta, w.leaf_seg);
     note_launch(3);
     prof_mark(ST_LEAVES, s);
 }
@@ -503,12 +552,12 @@ void stage_cells_leaves(const Work &w, float eps, int minpts, const Params &p, c
 void stage_hierarchy(const Work &w, cudaStream_t s)
 {
     cudaMemsetAsync(w.slot, 0xff, (size_t)w.n * sizeof(unsigned long long), s);
-    cudaMemsetAsync(&w.st->pad[1], 0, sizeof(int), s);  // frontier count
-    k_build_local<<<div_up(w.n, BUILD_CHUNK), BUILD_CHUNK, BUILD_SMEM, s>>>(w.st, w.delta, w.nodes, w.right_of,
-                                                                            w.frontier, &w.st->pad[1]);
-    k_build_global<<<grid_cap(w, w.n / 16 + 1, 256), 256, 0, s>>>(w.st, w.delta, w.nodes, w.slot, w.right_of,
-                                                                  w.frontier, &w.st->pad[1]);
-    k_ropes<<<grid_cap(w, 2 * w.n, 256), 256, 0, s>>>(w.st, w.nodes, w.right_of, w.dev_status);
+    k_build_local<<<div_up(w.n, BUILD_CHUNK), BUILD_CHUNK, BUILD_SMEM, s>>>(w.st, w.seg, w.leaf_seg, w.delta, w.nodes,
+                                                                            w.right_of, w.frontier,
+                                                                            &w.st->frontier_count);
+    k_build_global<<<grid_cap(w, w.n / 16 + 1, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.delta, w.nodes, w.slot,
+                                                                  w.right_of, w.frontier, &w.st->frontier_count);
+    k_ropes<<<grid_cap(w, 2 * w.n, 256), 256, 0, s>>>(w.st, w.nodes, w.right_of, w.leaf_seg, w.dev_status);
     note_launch(3);
     prof_mark(ST_BUILD, s);
 }

@@ -37,20 +37,38 @@ struct Work {
     unsigned char *core;             // [n] core flags
     int *bmin;                       // [n] smallest border index per cluster root
     unsigned long long *stats;       // traversal counters (profile mode 2) or null
+    // segments (independent point sets); a single clustering call has nseg = 1
+    int nseg;
+    int *seg_off;                    // [nseg + 1] device offsets (input and sorted order alike)
+    SegState *seg;                   // [nseg]
+    int *leaf_seg;                   // [n] segment of each leaf
+    float *seg_eps_in;               // [nseg] device copy of the caller's eps (batches)
+    int *seg_minpts_in;              // [nseg] device copy of the caller's minPts (batches)
+    bool any_fof, any_dbscan;        // host: which modes the call's segments use
     size_t sort_tiles, scan_tiles;
 };
 
-size_t work_bytes(int64_t n);
-void work_carve(Work &w, void *base, int64_t n);
+size_t work_bytes(int64_t n, int nseg = 1);
+void work_carve(Work &w, void *base, int64_t n, int nseg = 1);
 
-// Stages (all asynchronous on `s`).
-void stage_bounds_quant(const Work &w, const float *points, float eps, const Params &p, cudaStream_t s);
+// Segment parameters of a call, as the host gives them.
+struct SegHost {
+    int nseg;
+    const float *eps;      // host [nseg]
+    const int32_t *minpts; // host [nseg]
+};
+
+// Stages (all asynchronous on `s`).  Segment parameters (eps, minPts,
+// offsets) must already be in w.seg / w.seg_off: stage_segments_single puts
+// them there for a single clustering call.
+void stage_segments_single(const Work &w, float eps, int minpts, cudaStream_t s);
+void stage_segments_batch(const Work &w, const float *eps_dev, const int *minpts_dev, int seg_bits, cudaStream_t s);
+void stage_bounds_quant(const Work &w, const float *points, const Params &p, cudaStream_t s);
 void stage_morton_sort(const Work &w, const float *points, cudaStream_t s);
-void stage_gather(const Work &w, const float *points, int minpts, cudaStream_t s);
-void stage_cells_leaves(const Work &w, float eps, int minpts, const Params &p, cudaStream_t s);
+void stage_gather(const Work &w, const float *points, cudaStream_t s);
+void stage_cells_leaves(const Work &w, const Params &p, cudaStream_t s);
 void stage_hierarchy(const Work &w, cudaStream_t s);
-void stage_cluster(const Work &w, float eps, int minpts, const Params &p, int32_t *labels,
-                   cudaStream_t s);
+void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t s);
 
 // One-time per-device kernel attributes.
 void kernels_init_device();

@@ -232,3 +232,48 @@ def test_profile_api(abx):
     assert ms5["count"] > 0 and ms5["border"] > 0
     assert 1 <= c["radix_passes"] <= 8 and 1 <= c["leaves"] <= len(p) and c["morton_bits"] <= 21
     assert n1 - n0 >= 15
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_batch_many_uneven_segments(abx, seed):
+    """Hundreds of segments of uneven size, each with its own eps and minPts
+    (friends-of-friends and DBSCAN mixed in one call), must each equal the
+    oracle on that segment alone."""
+    rng = np.random.default_rng(100 + seed)
+    sizes = np.concatenate([[0, 1, 2, 0], rng.integers(1, 3000, 300), rng.integers(3000, 40000, 8)])
+    rng.shuffle(sizes)
+    segs, eps, mp = [], [], []
+    for k, n in enumerate(sizes):
+        if n == 0:
+            segs.append(np.zeros((0, 3), np.float32))
+        else:
+            p = _clumpy(rng, int(n), 4, 0.01)
+            if k % 3 == 0:  # a segment far from the unit box, scaled
+                p = (p * 50.0 - 20.0).astype(np.float32)
+            segs.append(p)
+        e = float(np.float32(rng.uniform(0.005, 0.03)))
+        eps.append(e * (50.0 if k % 3 == 0 else 1.0))
+        mp.append(int(rng.choice([1, 2, 3, 5, 10])))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    allp = torch.from_numpy(np.concatenate(segs).astype(np.float32)).cuda()
+    lab = abx.dbscan_batch(allp, off, eps, mp)
+    torch.cuda.synchronize()
+    assert abx.device_status() == 0
+    lab = lab.cpu().numpy()
+    for k in range(len(sizes)):
+        want = oracle.dbscan(segs[k], eps[k], mp[k])
+        assert_same(lab[off[k]:off[k + 1]], want, f"segment {k} (n={sizes[k]}, minPts={mp[k]})")
+
+
+def test_batch_of_stream_requests(abx):
+    """A batch shaped like the served stream: halo-like requests of
+    log-uniform size, minPts in {2, 5, 10}, eps from the linking length."""
+    from workloads import request_stream
+    reqs = [r for r in request_stream(60, n_hi=2e5)]
+    segs = [r.points() for r in reqs]
+    off = np.concatenate([[0], np.cumsum([len(p) for p in segs])]).astype(np.int64)
+    allp = torch.from_numpy(np.concatenate(segs)).cuda()
+    lab = abx.dbscan_batch(allp, off, [r.eps for r in reqs], [r.minpts for r in reqs]).cpu().numpy()
+    assert abx.device_status() == 0
+    for k, r in enumerate(reqs):
+        assert_same(lab[off[k]:off[k + 1]], oracle.dbscan(segs[k], r.eps, r.minpts), f"request {k}")
