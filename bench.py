@@ -152,6 +152,95 @@ def cpu_baseline(cfg, p: np.ndarray, frac_x: float) -> dict:
             "sample": f"{len(sel)} points with x < {frac_x} of the same workload ({dt:.1f} s, 1 thread)"}
 
 
+def served_benchmark(abx, n_requests: int, rate_hz: float) -> dict:
+    """The served stream (first n_requests of the 2,000-request stream: Poisson
+    arrivals, log-uniform sizes 10^3..10^7, halo mixture, minPts in {2,5,10})
+    replayed in real time through (a) the plain path -- one blocking
+    abx_dbscan_host per request, first come first served -- and (b) the
+    continuous-batching server; then both again with every request queued at
+    t = 0 (requests/s).  Latency = completion - arrival.  The labels of every
+    request must be identical on both paths."""
+    import threading
+
+    from workloads import request_stream
+    reqs = request_stream(2000, rate_hz=rate_hz)[:n_requests]
+    pts = [r.points() for r in reqs]
+    lib = abx.lib()
+    s_ptr = abx._stream(None)
+    plain_labels = [np.empty(len(p), np.int32) for p in pts]
+
+    def plain_one(k):
+        rc = lib.abx_dbscan_host(pts[k].ctypes.data, len(pts[k]), float(np.float32(reqs[k].eps)), reqs[k].minpts,
+                                 plain_labels[k].ctypes.data, s_ptr)
+        assert rc == 0, abx.status_str(rc)
+
+    plain_one(0)  # warm
+    # (a) plain, open loop
+    lat = []
+    t0 = time.perf_counter()
+    for k, r in enumerate(reqs):
+        wait = t0 + r.arrival_s - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        plain_one(k)
+        lat.append(time.perf_counter() - (t0 + r.arrival_s))
+    plain_open = {"p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                  "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3)}
+    t0 = time.perf_counter()
+    for k in range(len(reqs)):
+        plain_one(k)
+    plain_rps = len(reqs) / (time.perf_counter() - t0)
+
+    def served(open_loop: bool):
+        srv = abx.Server()
+        out = [None] * len(reqs)
+        tickets = [None] * len(reqs)
+        done_at = [0.0] * len(reqs)
+        ready = threading.Event()
+
+        def waiter():
+            ready.wait()
+            for k in range(len(reqs)):
+                while tickets[k] is None:
+                    time.sleep(0.0002)
+                st, lab = srv.wait(tickets[k], 300000)
+                assert st == 0, abx.status_str(st)
+                done_at[k] = time.perf_counter()
+                out[k] = lab
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        ready.set()
+        for k, r in enumerate(reqs):
+            if open_loop:
+                wait = t0 + r.arrival_s - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+            tickets[k] = srv.submit(pts[k], r.eps, r.minpts)
+        th.join()
+        st = srv.stats()
+        srv.close()
+        arr = [t0 + (r.arrival_s if open_loop else 0.0) for r in reqs]
+        lat = [d - a for d, a in zip(done_at, arr)]
+        return out, lat, st, max(done_at) - t0
+
+    out_o, lat_o, st_o, _ = served(True)
+    out_s, _, st_s, span = served(False)
+    exact = all(np.array_equal(a, b) for a, b in zip(plain_labels, out_o)) and \
+        all(np.array_equal(a, b) for a, b in zip(plain_labels, out_s))
+    return {"requests": len(reqs), "rate_hz": rate_hz, "points": int(sum(len(p) for p in pts)),
+            "sizes": "log-uniform 1e3..1e7, first requests of the seeded 2,000-request stream",
+            "plain": {**plain_open, "req_per_s": round(plain_rps, 2)},
+            "batched": {"p50_ms": round(1e3 * float(np.percentile(lat_o, 50)), 3),
+                        "p99_ms": round(1e3 * float(np.percentile(lat_o, 99)), 3),
+                        "req_per_s": round(len(reqs) / span, 2),
+                        "mean_batch_requests_open": round(st_o["mean_batch_requests"], 2),
+                        "mean_batch_requests_saturated": round(st_s["mean_batch_requests"], 2),
+                        "peak_hbm_bytes": int(st_s["peak_bytes"])},
+            "labels_identical": bool(exact)}
+
+
 def rank_config(base, rank: int, ws: int):
     """Replicas: rank r clusters its own instance of the workload (seed offset
     by 100 r); with one rank the workload is the configuration itself."""
@@ -220,6 +309,8 @@ def main():
     ap.add_argument("--cpu-frac", type=float, default=0.125)
     ap.add_argument("--ref-frac", type=float, default=0.0625)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--served-requests", type=int, default=120)
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_setup()
@@ -335,6 +426,10 @@ def main():
             "e2e": e2e, "roofline": roof, "pipeline": pipeline,
             "stage_ms": {k: round(v, 3) for k, v in mean_ms.items()}, "counters": counters,
             "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_served:
+        del t, labels
+        torch.cuda.synchronize()
+        line["served"] = served_benchmark(abx, args.served_requests, 200.0)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, p, args.cpu_frac)
     if rank == 0:

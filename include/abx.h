@@ -208,6 +208,75 @@ abx_status abx_profile_traversal(int64_t *out, int32_t n);
 /* Total number of kernels this library has launched in this process. */
 unsigned long long abx_launch_count(void);
 
+/* ---- serving: requests arriving over time, continuous batching ------------ */
+
+/*
+ * A server owns a scheduler thread and max_slots CUDA streams on one device.
+ * Requests (host points in, host labels out) queue in arrival order; whenever
+ * a slot is free the scheduler admits requests from the head of the queue
+ * into one batch -- as many as fit max_batch_requests, max_batch_points and
+ * the HBM budget left by batches still running -- and runs the batch as one
+ * abx_dbscan_batch pass on that slot's stream.  Batches admitted while others
+ * run overlap on the GPU.  A request's labels are exactly what abx_dbscan
+ * returns for it alone.  (North-star growth item: in-situ analysis of many
+ * sub-volumes; the paper itself clusters one rank's particles per call.)
+ */
+typedef struct abx_serve_config {
+    uint64_t hbm_budget_bytes;  /* device bytes running batches may hold (0 = 40 GiB) */
+    int32_t max_slots;          /* batches on the GPU at once, one stream each (0 = 2, max 16) */
+    int32_t max_batch_requests; /* most requests per batch (0 = 512) */
+    int64_t max_batch_points;   /* most points per batch (0 = 2^25) */
+    int32_t max_queue;          /* queued requests before submit returns ABX_EBUSY (0 = 2^20) */
+    int32_t device;             /* CUDA device ordinal */
+    int32_t reserved[4];
+} abx_serve_config;
+
+typedef struct abx_serve_report {
+    uint64_t submitted, completed, failed, cancelled;
+    uint64_t batches;            /* batches launched */
+    uint64_t queued;             /* requests waiting for admission */
+    uint64_t bytes_in_use;       /* device bytes reserved by running batches */
+    uint64_t peak_bytes;         /* highest bytes_in_use so far */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* latency: completion - submission */
+    double requests_per_s;       /* completed / (last completion - first submission) */
+    double mean_batch_requests;  /* requests per batch */
+} abx_serve_report;
+
+typedef struct abx_server abx_server;
+
+/* Create a server (cfg may be NULL for defaults).  Host-side fault injection
+ * for tests: ABX_SERVE_FAULT=hold admits nothing, =alloc fails every batch's
+ * device allocation (read at creation). */
+abx_status abx_serve_create(const abx_serve_config *cfg, abx_server **out);
+
+/*
+ * abx_serve_submit -- queue one request.  points: host float32 [n][3] and
+ * labels: host int32 [n], both caller-owned and left untouched by the caller
+ * until abx_serve_wait returns for the ticket.  Returns at once with a ticket;
+ * ABX_ENOMEM_BUDGET if the request alone exceeds the budget or the batch
+ * size, ABX_EBUSY if the queue is full, ABX_EINVAL for bad arguments.
+ */
+abx_status abx_serve_submit(abx_server *srv, const float *points, int64_t n, float eps, int32_t minpts,
+                            int32_t *labels, uint64_t *ticket);
+
+/*
+ * abx_serve_wait -- wait up to timeout_ms (< 0: forever) for a request:
+ * ABX_ETIMEOUT if it is not done yet (the ticket stays valid), else the
+ * request's status (ABX_OK, ABX_ECANCELLED, ABX_ENOMEM, ...), after which the
+ * ticket is released.
+ */
+abx_status abx_serve_wait(abx_server *srv, uint64_t ticket, int32_t timeout_ms);
+
+/* Counters and latency percentiles of the requests completed so far. */
+abx_status abx_serve_stats(abx_server *srv, abx_serve_report *out);
+
+/*
+ * abx_serve_destroy -- stop the server: queued requests end ABX_ECANCELLED,
+ * batches already on the GPU run to completion; then the streams and staging
+ * buffers are freed.  Must not run concurrently with other calls on srv.
+ */
+abx_status abx_serve_destroy(abx_server *srv);
+
 /* ---- the bounding volume hierarchy on its own ------------------------------ */
 
 /* Opaque, library-owned hierarchy over a point set (paper, section "ArborX

@@ -8,6 +8,7 @@ is missing or fails to load, every call raises.
 """
 from .binding import (  # noqa: F401
     ABX_EBUSY, ABX_ECANCELLED, ABX_ECUDA, ABX_EINTERNAL, ABX_EINVAL, ABX_ENOMEM, ABX_ENOMEM_BUDGET,
-    ABX_ENONFINITE, ABX_ETIMEOUT, ABX_OK, AbxError, BVH, Params, dbscan, dbscan_batch, dbscan_host,
+    ABX_ENONFINITE, ABX_ETIMEOUT, ABX_OK, AbxError, BVH, Params, Server, ServeConfig, dbscan, dbscan_batch,
+    dbscan_host,
     device_status, launch_count, lib, profile_enable, profile_read, status_str,
 )

@@ -34,6 +34,21 @@ class Params(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 4)]
 
 
+class ServeConfig(ctypes.Structure):
+    """abx_serve_config: 0 in any field = default (40 GiB, 2 slots, 512 requests,
+    2^25 points per batch, 2^20 queued)."""
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
+                ("max_batch_requests", ctypes.c_int32), ("max_batch_points", ctypes.c_int64),
+                ("max_queue", ctypes.c_int32), ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class ServeReport(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "failed", "cancelled", "batches",
+                                               "queued", "bytes_in_use", "peak_bytes")] + \
+               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "requests_per_s",
+                                               "mean_batch_requests")]
+
+
 _lock = threading.Lock()
 _lib = None
 _vp, _i64, _i32, _f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
@@ -56,6 +71,11 @@ _SIGS = {
     "abx_launch_count": (ctypes.c_uint64, []),
     "abx_profile_counters": (_i32, [_vp, _i32]),
     "abx_profile_traversal": (_i32, [_vp, _i32]),
+    "abx_serve_create": (_i32, [ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)]),
+    "abx_serve_submit": (_i32, [_vp, _vp, _i64, _f32, _i32, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "abx_serve_wait": (_i32, [_vp, ctypes.c_uint64, _i32]),
+    "abx_serve_stats": (_i32, [_vp, ctypes.POINTER(ServeReport)]),
+    "abx_serve_destroy": (_i32, [_vp]),
 }
 
 
@@ -222,6 +242,55 @@ class BVH:
         if self._h:
             _check(lib().abx_bvh_destroy(self._h), "abx_bvh_destroy")
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """abx_server: submit host point sets, wait for their labels.  The points
+    and label arrays of a request are kept alive here until it is waited for."""
+
+    def __init__(self, **cfg):
+        c = ServeConfig(**cfg)
+        self._h = ctypes.c_void_p()
+        _check(lib().abx_serve_create(ctypes.byref(c), ctypes.byref(self._h)), "abx_serve_create")
+        self._keep = {}
+
+    def submit(self, points: np.ndarray, eps: float, minpts: int) -> int:
+        p = np.ascontiguousarray(points, dtype=np.float32)
+        if p.ndim != 2 or p.shape[1] != 3:
+            raise TypeError("points must be float32 of shape (n, 3)")
+        lab = np.empty(p.shape[0], dtype=np.int32)
+        t = ctypes.c_uint64()
+        rc = lib().abx_serve_submit(self._h, p.ctypes.data, p.shape[0], float(np.float32(eps)), int(minpts),
+                                    lab.ctypes.data, ctypes.byref(t))
+        _check(rc, "abx_serve_submit")
+        self._keep[t.value] = (p, lab)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(status, labels): status ABX_OK with the labels, ABX_ETIMEOUT (ticket
+        still pending), or the request's error."""
+        rc = lib().abx_serve_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms))
+        if rc == ABX_ETIMEOUT:
+            return rc, None
+        _, lab = self._keep.pop(ticket, (None, None))
+        return rc, (lab if rc == ABX_OK else None)
+
+    def stats(self) -> dict:
+        r = ServeReport()
+        _check(lib().abx_serve_stats(self._h, ctypes.byref(r)), "abx_serve_stats")
+        return {k: getattr(r, k) for k, _ in ServeReport._fields_}
+
+    def close(self):
+        if self._h:
+            _check(lib().abx_serve_destroy(self._h), "abx_serve_destroy")
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:
