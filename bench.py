@@ -152,30 +152,42 @@ def cpu_baseline(cfg, p: np.ndarray, frac_x: float) -> dict:
             "sample": f"{len(sel)} points with x < {frac_x} of the same workload ({dt:.1f} s, 1 thread)"}
 
 
-def served_benchmark(abx, n_requests: int, rate_hz: float) -> dict:
+def served_benchmark(abx, n_requests: int, rate_hz: float, device: bool) -> dict:
     """The served stream (first n_requests of the 2,000-request stream: Poisson
     arrivals, log-uniform sizes 10^3..10^7, halo mixture, minPts in {2,5,10})
     replayed in real time through (a) the plain path -- one blocking
-    abx_dbscan_host per request, first come first served -- and (b) the
+    clustering call per request, first come first served -- and (b) the
     continuous-batching server; then both again with every request queued at
-    t = 0 (requests/s).  Latency = completion - arrival.  The labels of every
-    request must be identical on both paths."""
+    t = 0 (requests/s).  Latency = completion - arrival.  device=True keeps
+    every request's points and labels in HBM (the in-situ case: abx_dbscan per
+    request vs device-resident submissions); device=False starts from host
+    arrays (abx_dbscan_host vs host submissions).  The labels of every request
+    must be identical on both paths."""
     import threading
 
+    import torch
     from workloads import request_stream
     reqs = request_stream(2000, rate_hz=rate_hz)[:n_requests]
     pts = [r.points() for r in reqs]
     lib = abx.lib()
     s_ptr = abx._stream(None)
-    plain_labels = [np.empty(len(p), np.int32) for p in pts]
+    if device:
+        dpts = [torch.from_numpy(p).cuda() for p in pts]
+        plain_labels = [torch.empty(len(p), dtype=torch.int32, device="cuda") for p in pts]
+        torch.cuda.synchronize()
+    else:
+        plain_labels = [np.empty(len(p), np.int32) for p in pts]
 
     def plain_one(k):
-        rc = lib.abx_dbscan_host(pts[k].ctypes.data, len(pts[k]), float(np.float32(reqs[k].eps)), reqs[k].minpts,
-                                 plain_labels[k].ctypes.data, s_ptr)
-        assert rc == 0, abx.status_str(rc)
+        if device:
+            abx.dbscan(dpts[k], reqs[k].eps, reqs[k].minpts, labels=plain_labels[k])
+            torch.cuda.synchronize()
+        else:
+            rc = lib.abx_dbscan_host(pts[k].ctypes.data, len(pts[k]), float(np.float32(reqs[k].eps)),
+                                     reqs[k].minpts, plain_labels[k].ctypes.data, s_ptr)
+            assert rc == 0, abx.status_str(rc)
 
     plain_one(0)  # warm
-    # (a) plain, open loop
     lat = []
     t0 = time.perf_counter()
     for k, r in enumerate(reqs):
@@ -217,7 +229,7 @@ def served_benchmark(abx, n_requests: int, rate_hz: float) -> dict:
                 wait = t0 + r.arrival_s - time.perf_counter()
                 if wait > 0:
                     time.sleep(wait)
-            tickets[k] = srv.submit(pts[k], r.eps, r.minpts)
+            tickets[k] = srv.submit(dpts[k] if device else pts[k], r.eps, r.minpts)
         th.join()
         st = srv.stats()
         srv.close()
@@ -227,9 +239,14 @@ def served_benchmark(abx, n_requests: int, rate_hz: float) -> dict:
 
     out_o, lat_o, st_o, _ = served(True)
     out_s, _, st_s, span = served(False)
-    exact = all(np.array_equal(a, b) for a, b in zip(plain_labels, out_o)) and \
-        all(np.array_equal(a, b) for a, b in zip(plain_labels, out_s))
+
+    def same(a, b):
+        return bool(torch.equal(a, b)) if device else bool(np.array_equal(a, b))
+
+    exact = all(same(a, b) for a, b in zip(plain_labels, out_o)) and \
+        all(same(a, b) for a, b in zip(plain_labels, out_s))
     return {"requests": len(reqs), "rate_hz": rate_hz, "points": int(sum(len(p) for p in pts)),
+            "resident": "device (HBM)" if device else "host (pageable numpy)",
             "sizes": "log-uniform 1e3..1e7, first requests of the seeded 2,000-request stream",
             "plain": {**plain_open, "req_per_s": round(plain_rps, 2)},
             "batched": {"p50_ms": round(1e3 * float(np.percentile(lat_o, 50)), 3),
@@ -429,7 +446,8 @@ def main():
     if rank == 0 and ws == 1 and not args.no_served:
         del t, labels
         torch.cuda.synchronize()
-        line["served"] = served_benchmark(abx, args.served_requests, 200.0)
+        line["served"] = served_benchmark(abx, args.served_requests, 200.0, device=True)
+        line["served_host"] = served_benchmark(abx, args.served_requests, 200.0, device=False)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, p, args.cpu_frac)
     if rank == 0:

@@ -250,9 +250,11 @@ typedef struct abx_server abx_server;
 abx_status abx_serve_create(const abx_serve_config *cfg, abx_server **out);
 
 /*
- * abx_serve_submit -- queue one request.  points: host float32 [n][3] and
- * labels: host int32 [n], both caller-owned and left untouched by the caller
- * until abx_serve_wait returns for the ticket.  Returns at once with a ticket;
+ * abx_serve_submit -- queue one request.  points: float32 [n][3] and
+ * labels: int32 [n], both caller-owned, both host memory or both device
+ * memory of the server's device (device-resident requests, the in-situ case,
+ * skip the host staging), left untouched by the caller until abx_serve_wait
+ * returns for the ticket.  Returns at once with a ticket;
  * ABX_ENOMEM_BUDGET if the request alone exceeds the budget or the batch
  * size, ABX_EBUSY if the queue is full, ABX_EINVAL for bad arguments.
  */

@@ -260,14 +260,23 @@ class Server:
         _check(lib().abx_serve_create(ctypes.byref(c), ctypes.byref(self._h)), "abx_serve_create")
         self._keep = {}
 
-    def submit(self, points: np.ndarray, eps: float, minpts: int) -> int:
-        p = np.ascontiguousarray(points, dtype=np.float32)
-        if p.ndim != 2 or p.shape[1] != 3:
-            raise TypeError("points must be float32 of shape (n, 3)")
-        lab = np.empty(p.shape[0], dtype=np.int32)
+    def submit(self, points, eps: float, minpts: int) -> int:
+        """points: a numpy (n, 3) float32 array (host request) or a CUDA torch
+        tensor (device request); the labels come back on the same side."""
+        if hasattr(points, "is_cuda") and points.is_cuda:
+            import torch
+            p = _points_dev(points)
+            lab = torch.empty(p.shape[0], dtype=torch.int32, device=p.device)
+            pp, lp = p.data_ptr(), lab.data_ptr()
+        else:
+            p = np.ascontiguousarray(points, dtype=np.float32)
+            if p.ndim != 2 or p.shape[1] != 3:
+                raise TypeError("points must be float32 of shape (n, 3)")
+            lab = np.empty(p.shape[0], dtype=np.int32)
+            pp, lp = p.ctypes.data, lab.ctypes.data
         t = ctypes.c_uint64()
-        rc = lib().abx_serve_submit(self._h, p.ctypes.data, p.shape[0], float(np.float32(eps)), int(minpts),
-                                    lab.ctypes.data, ctypes.byref(t))
+        rc = lib().abx_serve_submit(self._h, pp, p.shape[0], float(np.float32(eps)), int(minpts), lp,
+                                    ctypes.byref(t))
         _check(rc, "abx_serve_submit")
         self._keep[t.value] = (p, lab)
         return t.value

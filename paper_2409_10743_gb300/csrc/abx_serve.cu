@@ -41,6 +41,7 @@ double now_s()
 
 struct Request {
     uint64_t ticket = 0;
+    bool on_device = false;   // points and labels are device memory
     const float *pts = nullptr;
     int64_t n = 0;
     float eps = 0.0f;
@@ -92,6 +93,29 @@ struct abx_server {
 
 namespace {
 
+// Host copies of large staging buffers are split over a few threads (one core
+// copies pageable memory far below what the host-device link carries).
+void par_memcpy(void *dst, const void *src, size_t bytes)
+{
+    const size_t chunk = (size_t)16 << 20;
+    if (bytes <= 2 * chunk) {
+        memcpy(dst, src, bytes);
+        return;
+    }
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nt = std::min<size_t>(std::min<size_t>(16, hw), (bytes + chunk - 1) / chunk);
+    const size_t per = (bytes + nt - 1) / nt;
+    std::vector<std::thread> ts;
+    for (size_t t = 1; t < nt; t++) {
+        const size_t a = t * per, b = std::min(bytes, a + per);
+        if (a < b)
+            ts.emplace_back([=] { memcpy((char *)dst + a, (const char *)src + a, b - a); });
+    }
+    memcpy(dst, src, std::min(bytes, per));
+    for (auto &t : ts)
+        t.join();
+}
+
 // Device bytes a batch of `n` points in `nseg` segments holds while it runs:
 // points and labels plus the pipeline's workspace.
 size_t batch_bytes(int64_t n, int nseg)
@@ -135,8 +159,8 @@ void finish_slot(abx_server *sv, Slot &sl)
     const abx_status st = sl.launch_rc;
     for (size_t k = 0; k < sl.reqs.size(); k++) {
         Request *r = sl.reqs[k];
-        if (st == ABX_OK)
-            memcpy(r->labels, sl.h_lab + sl.off[k], (size_t)r->n * sizeof(int32_t));
+        if (st == ABX_OK && !r->on_device)
+            par_memcpy(r->labels, sl.h_lab + sl.off[k], (size_t)r->n * sizeof(int32_t));
         finish_request(sv, r, st, t);
     }
     sv->bytes_in_use -= sl.reserved;
@@ -165,7 +189,10 @@ void launch_slot(abx_server *sv, Slot &sl)
         sl.minpts.push_back(r->minpts);
     }
     sl.total = sl.off.back();
-    if (sl.total > sl.cap) {
+    int64_t host_pts = 0;
+    for (Request *r : sl.reqs)
+        host_pts += r->on_device ? 0 : r->n;
+    if (host_pts > 0 && sl.total > sl.cap) {
         if (sl.h_pts)
             cudaFreeHost(sl.h_pts);
         if (sl.h_lab)
@@ -184,7 +211,8 @@ void launch_slot(abx_server *sv, Slot &sl)
     void *d_pts = nullptr, *d_lab = nullptr;
     if (sl.launch_rc == ABX_OK) {
         for (int k = 0; k < nseg; k++)
-            memcpy(sl.h_pts + 3 * sl.off[k], sl.reqs[k]->pts, (size_t)sl.reqs[k]->n * 3 * sizeof(float));
+            if (!sl.reqs[k]->on_device)
+                par_memcpy(sl.h_pts + 3 * sl.off[k], sl.reqs[k]->pts, (size_t)sl.reqs[k]->n * 3 * sizeof(float));
         if (sv->fault_alloc ||
             cudaMallocFromPoolAsync(&d_pts, (size_t)sl.total * 3 * sizeof(float), sv->pool, sl.stream) != cudaSuccess ||
             cudaMallocFromPoolAsync(&d_lab, (size_t)sl.total * sizeof(int32_t), sv->pool, sl.stream) != cudaSuccess) {
@@ -193,14 +221,25 @@ void launch_slot(abx_server *sv, Slot &sl)
         }
     }
     if (sl.launch_rc == ABX_OK) {
-        cudaMemcpyAsync(d_pts, sl.h_pts, (size_t)sl.total * 3 * sizeof(float), cudaMemcpyHostToDevice, sl.stream);
-        abx_status rc = abx_dbscan_batch(static_cast<const float *>(d_pts), sl.off.data(), nseg, sl.eps.data(),
-                                         sl.minpts.data(), static_cast<int32_t *>(d_lab),
+        float *dp = static_cast<float *>(d_pts);
+        int32_t *dl = static_cast<int32_t *>(d_lab);
+        for (int k = 0; k < nseg; k++) {  // gather the batch into one array
+            const Request *r = sl.reqs[k];
+            cudaMemcpyAsync(dp + 3 * sl.off[k], r->on_device ? r->pts : sl.h_pts + 3 * sl.off[k],
+                            (size_t)r->n * 3 * sizeof(float),
+                            r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sl.stream);
+        }
+        abx_status rc = abx_dbscan_batch(dp, sl.off.data(), nseg, sl.eps.data(), sl.minpts.data(), dl,
                                          reinterpret_cast<abx_stream>(sl.stream));
         if (rc != ABX_OK)
             sl.launch_rc = rc;
         else
-            cudaMemcpyAsync(sl.h_lab, d_lab, (size_t)sl.total * sizeof(int32_t), cudaMemcpyDeviceToHost, sl.stream);
+            for (int k = 0; k < nseg; k++) {  // and scatter the labels back
+                const Request *r = sl.reqs[k];
+                cudaMemcpyAsync(r->on_device ? r->labels : sl.h_lab + sl.off[k], dl + sl.off[k],
+                                (size_t)r->n * sizeof(int32_t),
+                                r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, sl.stream);
+            }
     }
     if (d_pts)
         cudaFreeAsync(d_pts, sl.stream);
@@ -343,7 +382,25 @@ abx_status abx_serve_submit(abx_server *sv, const float *points, int64_t n, floa
         return ABX_EINVAL;
     if (n > sv->cfg.max_batch_points || batch_bytes(n, 1) > sv->cfg.hbm_budget_bytes)
         return ABX_ENOMEM_BUDGET;
+    // device-resident requests (the in-situ case) skip the host staging
+    bool on_device = false;
+    if (n > 0) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, points) == cudaSuccess)
+            on_device = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+        else
+            cudaGetLastError();
+        cudaPointerAttributes b;
+        bool lab_dev = false;
+        if (cudaPointerGetAttributes(&b, labels) == cudaSuccess)
+            lab_dev = b.type == cudaMemoryTypeDevice || b.type == cudaMemoryTypeManaged;
+        else
+            cudaGetLastError();
+        if (lab_dev != on_device)
+            return ABX_EINVAL;  // points and labels must live on the same side
+    }
     Request *r = new Request();
+    r->on_device = on_device;
     r->pts = points;
     r->n = n;
     r->eps = eps;

@@ -56,6 +56,25 @@ def test_results_equal_alone_and_oracle(abx, requests):
         srv.close()
 
 
+def test_device_resident_requests(abx, requests):
+    """In-situ requests already in HBM: labels come back on the device, equal
+    to the alone-run, while host requests share the same batches."""
+    srv = abx.Server(max_slots=2)
+    try:
+        ts = []
+        for k, (r, p) in enumerate(requests[:20]):
+            src = torch.from_numpy(p).cuda() if k % 2 == 0 else p
+            ts.append((srv.submit(src, r.eps, r.minpts), r, p, k % 2 == 0))
+        for t, r, p, dev in ts:
+            st, lab = srv.wait(t, 60000)
+            assert st == abx.ABX_OK
+            got = lab.cpu().numpy() if dev else lab
+            assert (lab.is_cuda if dev else isinstance(lab, np.ndarray))
+            assert np.array_equal(got, _alone(abx, p, r.eps, r.minpts)), f"request {r.k}"
+    finally:
+        srv.close()
+
+
 def test_budget_limits_admission(abx, requests):
     budget = 96 << 20
     srv = abx.Server(hbm_budget_bytes=budget, max_slots=3)
