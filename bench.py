@@ -328,6 +328,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--served-requests", type=int, default=120)
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_setup()
@@ -353,6 +354,9 @@ def main():
     labels = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    tuned = None
+    if not args.no_autotune:  # part of warm-up: the autotuner's pick is used by every timed step
+        tuned = abx.autotune(t, cfg.eps, cfg.minpts)
     for _ in range(args.warmup):
         abx.dbscan(t, cfg.eps, cfg.minpts, labels=labels)
     torch.cuda.synchronize()
@@ -442,6 +446,7 @@ def main():
                        "l2": "no flush: inputs (1.6 GB) and working set exceed the 129 MB L2"},
             "e2e": e2e, "roofline": roof, "pipeline": pipeline,
             "stage_ms": {k: round(v, 3) for k, v in mean_ms.items()}, "counters": counters,
+            "params": tuned if tuned is not None else "library defaults",
             "gpu_launches": int(launches), "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_served:
         del t, labels

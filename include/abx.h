@@ -79,13 +79,16 @@ typedef struct CUstream_st *abx_stream;
  *   sub_bits     Morton bits per axis below the dense-cell side (1..8; -1 = none,
  *                the default)
  *   block        threads per block of the traversal kernels (64..1024, default 256)
+ *   dense_min    a cell is dense only with at least max(minPts, 2, dense_min)
+ *                points (0..1<<20, default 0)
  */
 typedef struct abx_params {
     int32_t leaf_size;
     int32_t dense_cells;
     int32_t sub_bits;
     int32_t block;
-    int32_t reserved[4];
+    int32_t dense_min;
+    int32_t reserved[3];
 } abx_params;
 
 /* Human-readable name of a status code (static storage). */
@@ -166,6 +169,43 @@ abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t
  */
 abx_status abx_dbscan_noalloc(const float *points, int64_t n, float eps, int32_t minpts,
                               int32_t *labels, abx_stream stream);
+
+/* ---- per-cluster statistics --------------------------------------------------- */
+
+/*
+ * abx_cluster_stats -- reduce a labelling (as abx_dbscan writes it) to its
+ * clusters, in increasing cluster id: ids[k] (the cluster's id), sizes[k],
+ * centres[k] = mean member position (summed in double, rounded to float) and
+ * radii[k] = distance from that centre to the farthest member (sqrtf of the
+ * largest exact FP32 squared distance) -- the galaxy circles of the paper's
+ * HACC section.  Noise (-1) is skipped; labels must lie in [-1, n).
+ *   points  device float32 [n][3];  labels device int32 [n]
+ *   ids, sizes device int32 [n];  centres device float32 [n][3];  radii device
+ *   float32 [n] (capacity n; the first *n_clusters entries are written)
+ *   n_clusters  host; the call waits for `stream`
+ */
+abx_status abx_cluster_stats(const float *points, const int32_t *labels, int64_t n, int32_t *n_clusters,
+                             int32_t *ids, int32_t *sizes, float *centres, float *radii, abx_stream stream);
+
+/* ---- autotuning (spec growth item; the paper lists runtime tuning of
+ *      occupancy parameters as future work, section "Conclusions") --------- */
+
+/*
+ * abx_autotune -- time candidate parameters on this input (leaf size, then
+ * traversal block size, then dense cells on/off and the minimum dense-cell
+ * size, keeping the best so far; each candidate once to warm up and twice
+ * timed with CUDA events on `stream`), remember the fastest for this device and
+ * size class (friends-of-friends or DBSCAN, floor(log2 n)), and return it in
+ * *best (may be NULL).  Later abx_dbscan calls of that class without explicit
+ * parameters use it.  labels (device int32 [n]) receives the labels.  Blocks.
+ */
+abx_status abx_autotune(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
+                        abx_params *best, abx_stream stream);
+
+/* The remembered parameters of the size class of (n, minpts) on the current
+ * device (ABX_EINVAL if none), and setting them (e.g. from a saved table). */
+abx_status abx_tune_get(int64_t n, int32_t minpts, abx_params *out);
+abx_status abx_tune_set(int64_t n, int32_t minpts, const abx_params *params);
 
 /* ---- stage timers (tracing) -------------------------------------------------- */
 
@@ -304,6 +344,19 @@ abx_status abx_bvh_build(const float *points, int64_t n, int32_t leaf_size, abx_
  */
 abx_status abx_bvh_count(const abx_bvh *bvh, const float *queries, int64_t nq, float eps,
                          int32_t cap, int32_t *counts, abx_stream stream);
+
+/*
+ * abx_bvh_pair_histogram -- the "find every pair within a radius, apply F"
+ * form of pair traversal (paper, subsection "Pair traversal": forces,
+ * 2-point correlation counts), with F = count by distance: hist[b] = number of
+ * unordered pairs {i, j}, i != j, of the tree's points with
+ * fl(r_b^2) < d2 <= fl(r_{b+1}^2), d2 the exact FP32 squared distance of the
+ * neighbour test.  Each pair is visited once.
+ *   r_edges  host float [nbins + 1], finite, >= 0, strictly increasing
+ *   nbins    1..256;  hist  device uint64 [nbins], overwritten
+ */
+abx_status abx_bvh_pair_histogram(const abx_bvh *bvh, const float *r_edges, int32_t nbins, uint64_t *hist,
+                                  abx_stream stream);
 
 /* Number of points, leaves and levels (depth of the deepest leaf + 1) of a
  * built hierarchy; waits for `stream`. */

@@ -55,6 +55,12 @@ def _load():
                                               ctypes.c_int32, ctypes.c_void_p]
             lib.oracle_pair_count.restype = ctypes.c_int64
             lib.oracle_pair_count.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_float]
+            lib.oracle_cluster_stats.restype = ctypes.c_int64
+            lib.oracle_cluster_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
+                [ctypes.c_void_p] * 4
+            lib.oracle_pair_histogram.restype = ctypes.c_int
+            lib.oracle_pair_histogram.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                                  ctypes.c_int32, ctypes.c_void_p]
             lib.oracle_pred.restype = ctypes.c_int
             lib.oracle_pred.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float]
             _lib = lib
@@ -113,3 +119,30 @@ def pred(p, q, eps: float) -> bool:
     a = np.ascontiguousarray(p, dtype=np.float32).reshape(3)
     b = np.ascontiguousarray(q, dtype=np.float32).reshape(3)
     return bool(_load().oracle_pred(a.ctypes.data, b.ctypes.data, float(np.float32(eps))))
+
+
+def cluster_stats(points, labels) -> dict:
+    """Per cluster (increasing id): ids, sizes, centres (k, 3), radii."""
+    p = _points(points)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    n = p.shape[0]
+    ids = np.empty(n, np.int32)
+    sizes = np.empty(n, np.int32)
+    cen = np.empty((n, 3), np.float32)
+    rad = np.empty(n, np.float32)
+    k = _load().oracle_cluster_stats(p.ctypes.data, lab.ctypes.data, n, ids.ctypes.data, sizes.ctypes.data,
+                                     cen.ctypes.data, rad.ctypes.data)
+    if k < 0:
+        raise OracleError(_ERRORS.get(int(k), f"error {k}"))
+    return {"ids": ids[:k], "sizes": sizes[:k], "centres": cen[:k], "radii": rad[:k]}
+
+
+def pair_histogram(points, r_edges) -> np.ndarray:
+    """hist[b] = unordered pairs with fl(r_b^2) < d2 <= fl(r_{b+1}^2)."""
+    p = _points(points)
+    e = np.ascontiguousarray(r_edges, dtype=np.float32)
+    h = np.zeros(e.size - 1, np.int64)
+    rc = _load().oracle_pair_histogram(p.ctypes.data, p.shape[0], e.ctypes.data, e.size - 1, h.ctypes.data)
+    if rc != 0:
+        raise OracleError(_ERRORS.get(rc, f"error {rc}"))
+    return h

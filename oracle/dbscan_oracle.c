@@ -471,3 +471,136 @@ int64_t oracle_pair_count(const float *points, int64_t n, float eps)
     free(g.s);
     return c.pairs;
 }
+
+/* ---- consumers of a clustering (plain definitions) ------------------------- */
+
+/*
+ * oracle_cluster_stats: per cluster id l (a label value >= 0), in increasing
+ * l: size, centre = mean position (summed in double in index order, rounded
+ * to float), radius = sqrtf of the largest FP32 squared distance (the
+ * predicate's expression) from that centre to a member.  Returns the number
+ * of clusters written, or a negative error.  The paper's HACC section draws
+ * galaxies as circles of that radius.
+ */
+int64_t oracle_cluster_stats(const float *points, const int32_t *labels, int64_t n, int32_t *ids, int32_t *sizes,
+                             float *centres, float *radii)
+{
+    if (n < 0)
+        return ORC_EINVAL;
+    int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    double *sum = (double *)calloc(3 * ((size_t)n + 1), sizeof(double));
+    float *r2 = (float *)calloc((size_t)n + 1, sizeof(float));
+    if (!cnt || !sum || !r2) {
+        free(cnt);
+        free(sum);
+        free(r2);
+        return ORC_ENOMEM;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        int32_t l = labels[i];
+        if (l < 0)
+            continue;
+        if (l >= n) {
+            free(cnt);
+            free(sum);
+            free(r2);
+            return ORC_EINVAL;
+        }
+        cnt[l]++;
+        for (int k = 0; k < 3; k++)
+            sum[3 * l + k] += (double)points[3 * i + k];
+    }
+    float *cen = (float *)malloc(3 * ((size_t)n + 1) * sizeof(float));
+    if (!cen) {
+        free(cnt);
+        free(sum);
+        free(r2);
+        return ORC_ENOMEM;
+    }
+    for (int64_t l = 0; l < n; l++)
+        if (cnt[l])
+            for (int k = 0; k < 3; k++)
+                cen[3 * l + k] = (float)(sum[3 * l + k] / (double)cnt[l]);
+    for (int64_t i = 0; i < n; i++) {
+        int32_t l = labels[i];
+        if (l < 0)
+            continue;
+        float dx = points[3 * i] - cen[3 * l];
+        float dy = points[3 * i + 1] - cen[3 * l + 1];
+        float dz = points[3 * i + 2] - cen[3 * l + 2];
+        float d2 = dx * dx + dy * dy;
+        d2 = d2 + dz * dz;
+        if (d2 > r2[l])
+            r2[l] = d2;
+    }
+    int64_t k = 0;
+    for (int64_t l = 0; l < n; l++)
+        if (cnt[l]) {
+            ids[k] = (int32_t)l;
+            sizes[k] = (int32_t)cnt[l];
+            for (int a = 0; a < 3; a++)
+                centres[3 * k + a] = cen[3 * l + a];
+            radii[k] = sqrtf(r2[l]);
+            k++;
+        }
+    free(cnt);
+    free(sum);
+    free(r2);
+    free(cen);
+    return k;
+}
+
+/*
+ * oracle_pair_histogram: hist[b] = number of unordered pairs {i, j}, i != j,
+ * with fl(r_b^2) < d2 <= fl(r_{b+1}^2), d2 the predicate's FP32 expression
+ * (paper, subsection "Pair traversal": apply F to every pair within a radius).
+ */
+typedef struct {
+    const float *pts;
+    const float *e2;
+    int nbins;
+    int64_t *hist;
+} orc_hist;
+
+static int visit_hist(void *ctx, int64_t i, int64_t j)
+{
+    orc_hist *h = (orc_hist *)ctx;
+    if (j <= i)
+        return 0;
+    const float *p = h->pts + 3 * i, *q = h->pts + 3 * j;
+    float dx = p[0] - q[0];
+    float dy = p[1] - q[1];
+    float dz = p[2] - q[2];
+    float d2 = dx * dx + dy * dy;
+    d2 = d2 + dz * dz;
+    for (int b = 0; b < h->nbins; b++)
+        if (d2 > h->e2[b] && d2 <= h->e2[b + 1]) {
+            h->hist[b]++;
+            break;
+        }
+    return 0;
+}
+
+int oracle_pair_histogram(const float *points, int64_t n, const float *r_edges, int32_t nbins, int64_t *hist)
+{
+    if (n < 0 || nbins < 1 || nbins > 256)
+        return ORC_EINVAL;
+    float e2[257];
+    for (int b = 0; b <= nbins; b++) {
+        if (!(r_edges[b] >= 0.0f) || isinf(r_edges[b]) || (b > 0 && !(r_edges[b] > r_edges[b - 1])))
+            return ORC_EINVAL;
+        e2[b] = r_edges[b] * r_edges[b];
+    }
+    for (int b = 0; b < nbins; b++)
+        hist[b] = 0;
+    if (n == 0)
+        return ORC_OK;
+    orc_grid g;
+    int rc = orc_build_grid(&g, points, n, r_edges[nbins]);
+    if (rc != ORC_OK)
+        return rc;
+    orc_hist h = {points, e2, nbins, hist};
+    orc_sweep(&g, want_all, visit_hist, &h);
+    free(g.s);
+    return ORC_OK;
+}

@@ -30,8 +30,8 @@ class AbxError(RuntimeError):
 class Params(ctypes.Structure):
     """abx_params: 0 in any field = library default; no field changes the labels."""
     _fields_ = [("leaf_size", ctypes.c_int32), ("dense_cells", ctypes.c_int32),
-                ("sub_bits", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("sub_bits", ctypes.c_int32), ("block", ctypes.c_int32), ("dense_min", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -71,6 +71,11 @@ _SIGS = {
     "abx_launch_count": (ctypes.c_uint64, []),
     "abx_profile_counters": (_i32, [_vp, _i32]),
     "abx_profile_traversal": (_i32, [_vp, _i32]),
+    "abx_cluster_stats": (_i32, [_vp, _vp, _i64, ctypes.POINTER(_i32), _vp, _vp, _vp, _vp, _vp]),
+    "abx_bvh_pair_histogram": (_i32, [_vp, _vp, _i32, _vp, _vp]),
+    "abx_autotune": (_i32, [_vp, _i64, _f32, _i32, _vp, ctypes.POINTER(Params), _vp]),
+    "abx_tune_get": (_i32, [_i64, _i32, ctypes.POINTER(Params)]),
+    "abx_tune_set": (_i32, [_i64, _i32, ctypes.POINTER(Params)]),
     "abx_serve_create": (_i32, [ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)]),
     "abx_serve_submit": (_i32, [_vp, _vp, _i64, _f32, _i32, _vp, ctypes.POINTER(ctypes.c_uint64)]),
     "abx_serve_wait": (_i32, [_vp, ctypes.c_uint64, _i32]),
@@ -171,6 +176,49 @@ def dbscan_batch(points, offsets, eps, minpts, labels=None, stream=None):
     return labels
 
 
+def autotune(points, eps: float, minpts: int, stream=None) -> dict:
+    """Time candidate parameters on this input; the winner is remembered for
+    its size class and returned as a dict."""
+    import torch
+    p = _points_dev(points)
+    lab = torch.empty(p.shape[0], dtype=torch.int32, device=p.device)
+    best = Params()
+    rc = lib().abx_autotune(p.data_ptr(), p.shape[0], float(np.float32(eps)), int(minpts), lab.data_ptr(),
+                            ctypes.byref(best), _stream(stream))
+    _check(rc, "abx_autotune")
+    return {k: getattr(best, k) for k in ("leaf_size", "dense_cells", "sub_bits", "block", "dense_min")}
+
+
+def tune_get(n: int, minpts: int):
+    p = Params()
+    return None if lib().abx_tune_get(int(n), int(minpts), ctypes.byref(p)) != ABX_OK else \
+        {k: getattr(p, k) for k in ("leaf_size", "dense_cells", "sub_bits", "block", "dense_min")}
+
+
+def tune_set(n: int, minpts: int, params: dict) -> None:
+    _check(lib().abx_tune_set(int(n), int(minpts), ctypes.byref(Params(**params))), "abx_tune_set")
+
+
+def cluster_stats(points, labels, stream=None) -> dict:
+    """Per cluster (increasing id): ids, sizes, centres (k, 3), radii -- torch
+    tensors on the points' device."""
+    import torch
+    p = _points_dev(points)
+    lab = labels.contiguous()
+    n = p.shape[0]
+    dev = p.device
+    ids = torch.empty(n, dtype=torch.int32, device=dev)
+    sizes = torch.empty(n, dtype=torch.int32, device=dev)
+    cen = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    rad = torch.empty(n, dtype=torch.float32, device=dev)
+    k = _i32()
+    rc = lib().abx_cluster_stats(p.data_ptr(), lab.data_ptr(), n, ctypes.byref(k), ids.data_ptr(), sizes.data_ptr(),
+                                 cen.data_ptr(), rad.data_ptr(), _stream(stream))
+    _check(rc, "abx_cluster_stats")
+    K = k.value
+    return {"ids": ids[:K], "sizes": sizes[:K], "centres": cen[:K], "radii": rad[:K]}
+
+
 def device_status(stream=None) -> int:
     """Wait for the stream; return and clear the device status word."""
     return int(lib().abx_device_status(_stream(stream)))
@@ -219,6 +267,7 @@ class BVH:
         p = _points_dev(points)
         self._h = ctypes.c_void_p()
         self._stream = _stream(stream)
+        self._points = p  # the build reads the points asynchronously
         rc = lib().abx_bvh_build(p.data_ptr(), p.shape[0], int(leaf_size), ctypes.byref(self._h), self._stream)
         _check(rc, "abx_bvh_build")
 
@@ -231,6 +280,15 @@ class BVH:
                                  out.data_ptr(), self._stream)
         _check(rc, "abx_bvh_count")
         return out
+
+    def pair_histogram(self, r_edges):
+        """hist[b] = unordered pairs with fl(r_b^2) < d2 <= fl(r_{b+1}^2)."""
+        import torch
+        e = np.ascontiguousarray(r_edges, dtype=np.float32)
+        h = torch.empty(e.size - 1, dtype=torch.int64, device="cuda")
+        rc = lib().abx_bvh_pair_histogram(self._h, e.ctypes.data, e.size - 1, h.data_ptr(), self._stream)
+        _check(rc, "abx_bvh_pair_histogram")
+        return h
 
     def info(self):
         n, L, lev = _i64(), _i64(), _i32()

@@ -177,14 +177,20 @@ void work_carve(Work &w, void *base, int64_t n, int nseg)
     w.any_fof = w.any_dbscan = false;
 }
 
-static abx_status resolve_params(const abx_params *in, Params &p)
+abx_status resolve_params(const abx_params *in, Params &p)
 {
     p.leaf_size = 4;
     p.dense = 1;
     p.sub_bits = 0;
     p.block = 256;
+    p.dense_min = 0;
     if (!in)
         return ABX_OK;
+    if (in->dense_min) {
+        if (in->dense_min < 0 || in->dense_min > (1 << 20))
+            return ABX_EINVAL;
+        p.dense_min = in->dense_min;
+    }
     if (in->leaf_size) {
         if (in->leaf_size < 1 || in->leaf_size > 32)
             return ABX_EINVAL;
@@ -275,6 +281,9 @@ abx_status abx_dbscan_ex(const float *points, int64_t n, float eps, int32_t minp
     if (rc != ABX_OK)
         return rc;
     Params p;
+    abx_params tuned;
+    if (!params && n > 0 && tune_lookup(n, minpts, &tuned))
+        params = &tuned;  // the autotuner's choice for this size class
     if ((rc = resolve_params(params, p)) != ABX_OK)
         return rc;
     if (n == 0)

@@ -12,12 +12,6 @@ abx_status bvh_device_ctx(cudaMemPool_t *pool, unsigned **status, int *n_sms);
 
 using namespace abx;
 
-struct abx_bvh {
-    void *ws;
-    Work w;
-    cudaStream_t stream;
-    cudaMemPool_t pool;
-};
 
 namespace abx {
 
@@ -101,7 +95,7 @@ abx_status abx_bvh_build(const float *points, int64_t n, int32_t leaf_size, abx_
     work_carve(h->w, h->ws, n);
     h->w.n_sms = n_sms;
     h->w.dev_status = status;
-    Params p{leaf_size ? leaf_size : 4, 0, 0, 256};
+    Params p{leaf_size ? leaf_size : 4, 0, 0, 256, 0};
     h->w.any_fof = true;
     stage_segments_single(h->w, 0.0f, 2, s);
     stage_bounds_quant(h->w, points, p, s);

@@ -90,7 +90,7 @@ extern "C" abx_status abx_dbscan_noalloc(const float *points, int64_t n, float e
     w.dev_status = d->status;
     w.any_fof = minpts <= 2;
     w.any_dbscan = !w.any_fof;
-    const Params p{4, 1, 0, 256};
+    const Params p{4, 1, 0, 256, 0};
     stage_segments_single(w, eps, minpts, s);
     stage_bounds_quant(w, points, p, s);
     stage_morton_sort(w, points, s);

@@ -148,6 +148,27 @@ __global__ void __launch_bounds__(256) k_bounds(const float *__restrict__ pts, i
         atomicOr(dev_status, DEV_NONFINITE);
 }
 
+// Large single segments: the bounds only place the grid (the Morton kernel
+// clamps points outside them and checks every coordinate for finiteness), so
+// a strided sample of the points is enough.
+__global__ void __launch_bounds__(256) k_bounds_sample(const float *__restrict__ pts, int64_t n, int stride,
+                                                       SegState *seg)
+{
+    MinMax m;
+    m.init();
+    const int64_t ns = (n + stride - 1) / stride;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ns; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k * stride;
+        m.upd(0, __ldg(pts + 3 * i));
+        m.upd(1, __ldg(pts + 3 * i + 1));
+        m.upd(2, __ldg(pts + 3 * i + 2));
+    }
+    // non-finite samples are ignored here (the Morton kernel flags them)
+    m.warp_reduce();
+    if ((threadIdx.x & 31) == 0 && m.mn0 <= m.mx0)
+        m.publish(seg[0]);
+}
+
 // Many segments: one point per lane; a warp whose points share a segment
 // reduces first and publishes once, otherwise every lane publishes.
 __global__ void __launch_bounds__(256) k_bounds_seg(const float *__restrict__ pts, int64_t n, SegState *seg,
@@ -243,8 +264,9 @@ __global__ void k_quant(State *st, SegState *seg, int nseg, int dense_on, int su
 template <bool SEG>
 __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ pts, int64_t n, State *st,
                                                 const SegState *__restrict__ seg, const int *__restrict__ off,
-                                                unsigned long long *__restrict__ keys)
+                                                unsigned long long *__restrict__ keys, unsigned *dev_status)
 {
+    bool bad = false;
     __shared__ unsigned sh[MAX_PASSES * RADIX];
     for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x)
         sh[i] = 0;
@@ -269,6 +291,7 @@ __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ pts, i
             top = (unsigned long long)s << shift;
         }
         float x = __ldg(pts + 3 * i), y = __ldg(pts + 3 * i + 1), z = __ldg(pts + 3 * i + 2);
+        bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
         float tx = (x - lx) * is, ty = (y - ly) * is, tz = (z - lz) * is;
         unsigned qx = tx < qmax ? (unsigned)fmaxf(tx, 0.0f) : (unsigned)qmax;
         unsigned qy = ty < qmax ? (unsigned)fmaxf(ty, 0.0f) : (unsigned)qmax;
@@ -278,6 +301,8 @@ __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ pts, i
         for (int p = 0; p < np; p++)
             atomicAdd(&sh[p * RADIX + (unsigned)((key >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
     }
+    if (bad)
+        atomicOr(dev_status, DEV_NONFINITE);
     __syncthreads();
     for (int i = threadIdx.x; i < np * RADIX; i += blockDim.x)
         if (sh[i])
@@ -554,8 +579,13 @@ void stage_segments_batch(const Work &w, const float *eps_dev, const int *minpts
 void stage_bounds_quant(const Work &w, const float *points, const Params &p, cudaStream_t s)
 {
     if (w.nseg == 1) {
-        int aligned = (reinterpret_cast<uintptr_t>(points) & 15) == 0;
-        k_bounds<<<grid_for(w, (3 * w.n + 3) / 4, 256), 256, 0, s>>>(points, w.n, aligned, w.seg, w.dev_status);
+        if (w.n >= (1 << 22)) {
+            k_bounds_sample<<<grid_for(w, w.n / 32, 256), 256, 0, s>>>(points, w.n, 32, w.seg);
+        } else {
+            int aligned = (reinterpret_cast<uintptr_t>(points) & 15) == 0;
+            k_bounds<<<grid_for(w, (3 * w.n + 3) / 4, 256), 256, 0, s>>>(points, w.n, aligned, w.seg,
+                                                                          w.dev_status);
+        }
     } else {
         k_bounds_seg<<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.seg, w.seg_off, w.nseg, w.dev_status);
     }
@@ -567,9 +597,11 @@ void stage_bounds_quant(const Work &w, const float *points, const Params &p, cud
 void stage_morton_sort(const Work &w, const float *points, cudaStream_t s)
 {
     if (w.nseg == 1)
-        k_morton<false><<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0]);
+        k_morton<false><<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0],
+                                                              w.dev_status);
     else
-        k_morton<true><<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0]);
+        k_morton<true><<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0],
+                                                             w.dev_status);
     note_launch();
     prof_mark(ST_MORTON, s);
     k_sort_plan<<<1, RADIX, 0, s>>>(w.st, w.n);

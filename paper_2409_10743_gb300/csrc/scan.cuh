@@ -1,0 +1,114 @@
+// Single-pass stream compaction of flagged positions (decoupled look-back).
+#pragma once
+
+#include "work.cuh"
+
+namespace abx {
+
+// ---- single-pass flag scan (decoupled look-back) --------------------------------
+// ids[k] = number of flagged positions <= k, minus one; first[id] = k for each
+// flagged k; first[total] = n; *total_out = total.
+
+constexpr unsigned long long SLB_AGG = 1ull << 62;
+constexpr unsigned long long SLB_PRE = 2ull << 62;
+
+__device__ __forceinline__ unsigned long long sld(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sst(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <class F>
+__global__ void __launch_bounds__(SCAN_THREADS) k_flag_scan(int64_t n, F f, int *ids, int *first, int *total_out,
+                                                            unsigned *tile_ctr, unsigned long long *lb,
+                                                            unsigned *dev_status, const State *st, int need_dense)
+{
+    if (need_dense && !st->dense_ok)
+        return;
+    __shared__ int s_tile;
+    __shared__ unsigned s_wsum[SCAN_THREADS / 32];
+    __shared__ unsigned long long s_excl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0)
+        s_tile = (int)atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    const int64_t base = (int64_t)tile * SCAN_TILE + (int64_t)tid * SCAN_ITEMS;
+    unsigned flags = 0;  // bit j = flag of item j
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        int64_t pos = base + j;
+        if (pos < n && f(pos))
+            flags |= 1u << j;
+    }
+    unsigned c = __popc(flags);
+    unsigned x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(~0u, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        s_wsum[warp] = x;
+    __syncthreads();
+    unsigned wpre = 0, total = 0;
+    for (int w = 0; w < SCAN_THREADS / 32; w++) {
+        if (w < warp)
+            wpre += s_wsum[w];
+        total += s_wsum[w];
+    }
+    if (tid == 0) {
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            sst(lb, SLB_PRE | total);
+        } else {
+            sst(lb + tile, SLB_AGG | total);
+            for (int t = tile - 1; t >= 0; t--) {
+                unsigned long long v;
+                int spins = 0;
+                while (true) {
+                    v = sld(lb + t);
+                    if ((v >> 62) != 0)
+                        break;
+                    if (++spins > SPIN_LIMIT) {
+                        atomicOr(dev_status, DEV_TIMEOUT);
+                        v = SLB_PRE;
+                        break;
+                    }
+                    if (spins > 64)
+                        __nanosleep(64);
+                }
+                excl += v & ((1ull << 62) - 1);
+                if ((v >> 62) == 2)
+                    break;
+            }
+            sst(lb + tile, SLB_PRE | (excl + total));
+        }
+        s_excl = excl;
+    }
+    __syncthreads();
+    unsigned long long run = s_excl + wpre + x - c;  // flags before this thread's first item
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        int64_t pos = base + j;
+        if (pos < n) {
+            if (flags & (1u << j)) {
+                first[run] = (int)pos;
+                run++;
+            }
+            ids[pos] = (int)run - 1;
+            if (pos == n - 1) {
+                first[run] = (int)n;
+                *total_out = (int)run;
+            }
+        }
+    }
+}
+
+}  // namespace abx

@@ -11,6 +11,7 @@ struct Params {
     int dense;       // dense-cell leaves on/off
     int sub_bits;    // Morton bits per axis below the dense-cell side
     int block;       // threads per block of the traversal kernels
+    int dense_min;   // a dense cell needs at least max(minPts, 2, dense_min) points
 };
 
 // Device buffers of one call; sizes are for n points (L <= n leaves).
@@ -70,6 +71,10 @@ void stage_cells_leaves(const Work &w, const Params &p, cudaStream_t s);
 void stage_hierarchy(const Work &w, cudaStream_t s);
 void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t s);
 
+// Parameter resolution (0 fields = defaults) and the autotuner's table.
+abx_status resolve_params(const abx_params *in, Params &p);
+bool tune_lookup(int64_t n, int32_t minpts, abx_params *out);
+
 // One-time per-device kernel attributes.
 void kernels_init_device();
 void tree_init_device();
@@ -87,3 +92,11 @@ void note_launch(int k = 1);
 __host__ __device__ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace abx
+
+// The hierarchy handle of the C ABI: the workspace of a build, kept alive.
+struct abx_bvh {
+    void *ws;
+    abx::Work w;
+    cudaStream_t stream;
+    cudaMemPool_t pool;
+};

@@ -121,3 +121,24 @@ def fof_components(p: np.ndarray, eps: float, block: int = 2048) -> np.ndarray:
     lab = first[comp]
     lab[deg < 2] = -1
     return lab.astype(np.int32)
+
+
+def pair_histogram(p: np.ndarray, r_edges, block: int = 1024) -> np.ndarray:
+    """Unordered pairs {i, j}, i != j, with fl(r_b^2) < d2 <= fl(r_{b+1}^2)."""
+    p = np.asarray(p, dtype=np.float32)
+    e = np.asarray(r_edges, dtype=np.float32)
+    e2 = e * e
+    n = len(p)
+    hist = np.zeros(len(e) - 1, np.int64)
+    for s in range(0, n, block):
+        q = p[s:s + block]
+        dx = q[:, None, 0] - p[None, :, 0]
+        dy = q[:, None, 1] - p[None, :, 1]
+        dz = q[:, None, 2] - p[None, :, 2]
+        d2 = (dx * dx + dy * dy) + dz * dz
+        i = np.arange(s, s + len(q))[:, None]
+        j = np.arange(n)[None, :]
+        d = d2[j > i]
+        for b in range(len(e) - 1):
+            hist[b] += int(((d > e2[b]) & (d <= e2[b + 1])).sum())
+    return hist

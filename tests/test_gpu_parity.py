@@ -277,3 +277,63 @@ def test_batch_of_stream_requests(abx):
     assert abx.device_status() == 0
     for k, r in enumerate(reqs):
         assert_same(lab[off[k]:off[k + 1]], oracle.dbscan(segs[k], r.eps, r.minpts), f"request {k}")
+
+
+def test_sampled_bounds_large_input_with_outliers(abx):
+    """Inputs of 2^22 points and more place the grid from a sample of the
+    points; outliers the sample misses are clamped into the grid, which never
+    changes a label; a non-finite coordinate anywhere is still reported."""
+    rng = np.random.default_rng(21)
+    n = (1 << 22) + 5
+    p = clumps(n, 4000, 21, a0=0.002)
+    far = rng.integers(0, n, 7)
+    p[far] = np.array([[5.0, -3.0, 9.0]], np.float32) + rng.random((7, 3)).astype(np.float32) * 1e-4
+    eps = float(np.float32(0.168 * n ** (-1 / 3)))
+    assert_same(gpu_labels(abx, p, eps, 2), oracle.dbscan(p, eps, 2), "outliers")
+    q = p.copy()
+    q[n - 3, 2] = np.inf
+    abx.dbscan(torch.from_numpy(q).cuda(), eps, 2)
+    assert abx.device_status() == abx.ABX_ENONFINITE
+
+
+def test_autotune_choice_is_used_and_labels_unchanged(abx, tmp_path):
+    from paper_2409_10743_gb300 import autotune
+    p = clumps(400_000, 400, 61, a0=0.02)
+    eps = 0.003
+    want = oracle.dbscan(p, eps, 5)
+    t = torch.from_numpy(p).cuda()
+    best = abx.autotune(t, eps, 5)
+    assert best["leaf_size"] in (2, 4, 8) and best["block"] in (0, 128, 256, 512)
+    assert abx.tune_get(len(p), 5) == best
+    assert_same(abx.dbscan(t, eps, 5).cpu().numpy(), want, "tuned")
+    path = str(tmp_path / "tune.json")
+    autotune.save(path)
+    abx.tune_set(len(p), 5, {"leaf_size": 2, "block": 128, "dense_cells": -1, "sub_bits": 0, "dense_min": 0})
+    assert_same(abx.dbscan(t, eps, 5).cpu().numpy(), want, "set")
+    assert autotune.load(path) >= 1 and abx.tune_get(len(p), 5) == best
+    with pytest.raises(abx.AbxError):
+        abx.tune_set(len(p), 5, {"leaf_size": 99})
+
+
+@pytest.mark.parametrize("minpts", [2, 5])
+def test_cluster_stats_match_oracle(abx, minpts):
+    p = clumps(300_000, 300, 71, a0=0.02)
+    eps = 0.004
+    t = torch.from_numpy(p).cuda()
+    lab = abx.dbscan(t, eps, minpts)
+    s = abx.cluster_stats(t, lab)
+    want = oracle.cluster_stats(p, lab.cpu().numpy())
+    assert np.array_equal(s["ids"].cpu().numpy(), want["ids"])
+    assert np.array_equal(s["sizes"].cpu().numpy(), want["sizes"])
+    # centres: double sums in another order, rounded to float: within 1 ulp
+    np.testing.assert_allclose(s["centres"].cpu().numpy(), want["centres"], rtol=1.2e-7, atol=0)
+    np.testing.assert_allclose(s["radii"].cpu().numpy(), want["radii"], rtol=2e-6, atol=1e-7)
+
+
+def test_pair_histogram_matches_oracle(abx):
+    p = clumps(200_000, 200, 81, a0=0.02)
+    edges = np.array([0.0, 0.001, 0.002, 0.004, 0.006, 0.01], np.float32)
+    h = abx.BVH(torch.from_numpy(p).cuda(), leaf_size=4)
+    got = h.pair_histogram(edges).cpu().numpy()
+    h.close()
+    assert np.array_equal(got, oracle.pair_histogram(p, edges))

@@ -208,8 +208,10 @@ def test_errors():
 
 MUTATIONS = [
     ("open neighbourhood", "return d2 <= e2;", "return d2 < e2;"),
-    ("dropped z term", "d2 = d2 + dz * dz;", "d2 = d2 + 0.0f * dz;"),
-    ("wrong sign in dy", "float dy = p[1] - q[1];", "float dy = p[1] + q[1];"),
+    ("dropped z term", "    d2 = d2 + dz * dz;\n    return d2 <= e2;", "    d2 = d2 + 0.0f * dz;\n    return d2 <= e2;"),
+    ("wrong sign in dy", "float dy = p[1] - q[1];\n    float dz = p[2] - q[2];\n    float d2 = dx * dx + dy * dy;\n"
+     "    d2 = d2 + dz * dz;\n    return d2 <= e2;", "float dy = p[1] + q[1];\n    float dz = p[2] - q[2];\n"
+     "    float d2 = dx * dx + dy * dy;\n    d2 = d2 + dz * dz;\n    return d2 <= e2;"),
     ("row offset off by one", "int64_t y = cy + (r % 3) - 1;", "int64_t y = cy + (r % 3);"),
     ("cell too small", "H *= 1.0 + ldexp(1.0, -10);", "H *= 0.5;"),
     ("core strict", "st.core[i] = st.count[i] >= minpts;", "st.core[i] = st.count[i] > minpts;"),
