@@ -46,10 +46,11 @@ def stage_bytes(stage: str, c: dict, n: int) -> float:
     P = max(1, c.get("radix_passes", 6))
     L = max(1, c.get("leaves", n // 4))
     per_leaf = L / n
+    kb = 4.0 if c.get("key_bits", 64) == 32 else 8.0  # key bytes
     table = {
         "bounds": 12.0,                                   # read xyz
-        "morton": 12.0 + 8.0,                             # read xyz, write key
-        "sort": 20.0 + (P - 1) * 24.0,                    # 1st pass: key in, key+idx out; then 24/pass
+        "morton": 12.0 + kb,                              # read xyz, write key
+        "sort": (kb + kb + 4.0) + (P - 1) * 2 * (kb + 4.0),  # 1st pass: key in, key+idx out; then both ways
         "gather": 4.0 + 12.0 + 16.0 + 4.0 + 1.0,          # perm, xyz, sorted float4, parent, core
         "cells": 8.0 + 4.0,                               # keys, dense-root preset
         "leaves": 4.0 + 4.0 + 16.0 + per_leaf * (32.0 + 16.0 + 1.0),  # dense root, leaf id, points; leaf records

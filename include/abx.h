@@ -234,7 +234,7 @@ abx_status abx_profile_read(float *ms, int32_t n);
  * abx_profile_counters -- facts about the most recent profiled clustering
  * call, written to out[0 .. n-1] in this order: radix passes run, Morton bits
  * per axis, dense cells on (0/1), dense cells found, hierarchy leaves, root
- * node.
+ * node, key width in bits (32 or 64).
  */
 abx_status abx_profile_counters(int64_t *out, int32_t n);
 

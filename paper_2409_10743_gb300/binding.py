@@ -250,9 +250,10 @@ def profile_read() -> dict:
 def profile_counters() -> dict:
     """Radix passes, Morton bits per axis, dense on, cells, leaves, root of the
     most recent profiled call."""
-    v = np.zeros(6, dtype=np.int64)
-    _check(lib().abx_profile_counters(v.ctypes.data, 6), "abx_profile_counters")
-    return dict(zip(["radix_passes", "morton_bits", "dense_on", "dense_cells", "leaves", "root"], map(int, v)))
+    v = np.zeros(7, dtype=np.int64)
+    _check(lib().abx_profile_counters(v.ctypes.data, 7), "abx_profile_counters")
+    return dict(zip(["radix_passes", "morton_bits", "dense_on", "dense_cells", "leaves", "root", "key_bits"],
+                    map(int, v)))
 
 
 def launch_count() -> int:

@@ -448,8 +448,8 @@ abx_status abx_profile_counters(int64_t *out, int32_t n)
     if (cudaStreamSynchronize(g_prof_stream) != cudaSuccess)
         return ABX_ECUDA;
     const State &st = *g_prof_state;
-    int64_t v[6] = {st.n_active, st.bits, st.dense_ok, st.n_cells, st.n_leaves, st.root};
-    for (int i = 0; i < n && i < 6; i++)
+    int64_t v[7] = {st.n_active, st.bits, st.dense_ok, st.n_cells, st.n_leaves, st.root, st.key32 ? 32 : 64};
+    for (int i = 0; i < n && i < 7; i++)
         out[i] = v[i];
     return ABX_OK;
 }

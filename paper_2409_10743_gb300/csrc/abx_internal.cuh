@@ -59,8 +59,78 @@ struct State {
     int root;                   // root of the whole hierarchy
     int frontier_count;         // nodes finishing the build in its global phase
     int bits;                   // Morton bits per axis of segment 0 (diagnostics)
-    int pad[3];
+    int key32;                  // keys fit 32 bits and are sorted as 32-bit words
+    int allow32;                // the call launched the 32-bit key kernels
+    int pad[1];
 };
+
+// Sorted key k, from whichever buffer the last radix pass wrote, whatever the
+// key width of the call.
+__device__ __forceinline__ unsigned long long sorted_key(const State *st, const void *k0, const void *k1, int64_t k)
+{
+    const void *buf = (st->n_active & 1) ? k1 : k0;
+    return st->key32 ? (unsigned long long)static_cast<const unsigned *>(buf)[k]
+                     : static_cast<const unsigned long long *>(buf)[k];
+}
+
+// ---- decoupled look-back ------------------------------------------------------
+// Status words: bits 62-63 = 0 (not published), 1 (the tile's own count), 2
+// (inclusive prefix through that tile); bits 0-61 = the count.  A tile sums
+// its predecessors' words backwards until an inclusive prefix.  The words of
+// a window of predecessors are loaded at once (one memory round trip per
+// window instead of per tile); a word not yet published is re-read with a
+// bounded spin.
+constexpr unsigned long long LB_FLAG_AGG = 1ull << 62;
+constexpr unsigned long long LB_FLAG_PRE = 2ull << 62;
+constexpr unsigned long long LB_COUNT = (1ull << 62) - 1;
+
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void lb_store(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Sum of the counts of tiles [0, tile) in column `slot` of a look-back array
+// with `stride` words per tile, LOOKBACK_WINDOW words per round trip.
+template <int LOOKBACK_WINDOW>
+__device__ __forceinline__ unsigned long long lookback(const unsigned long long *lb, int tile, int stride, int slot,
+                                                       unsigned *dev_status)
+{
+    unsigned long long excl = 0;
+    int t = tile - 1;
+    int spins = 0;
+    while (t >= 0) {
+        unsigned long long v[LOOKBACK_WINDOW];
+#pragma unroll
+        for (int k = 0; k < LOOKBACK_WINDOW; k++)
+            v[k] = t - k >= 0 ? lb_load(lb + (size_t)(t - k) * stride + slot) : LB_FLAG_PRE;
+        int k = 0;
+#pragma unroll
+        for (; k < LOOKBACK_WINDOW; k++) {
+            const unsigned long long f = v[k] >> 62;
+            if (f == 0)
+                break;  // tile t - k has not published yet
+            excl += v[k] & LB_COUNT;
+            if (f == 2)
+                return excl;
+        }
+        t -= k;
+        if (k < LOOKBACK_WINDOW) {
+            if (++spins > SPIN_LIMIT) {
+                atomicOr(dev_status, DEV_TIMEOUT);
+                return excl;
+            }
+            if (spins > 8)
+                __nanosleep(32);
+        }
+    }
+    return excl;
+}
 
 // Segment of input index i: the largest s with off[s] <= i (empty segments
 // are skipped because their successor has the same offset).

@@ -177,8 +177,7 @@ __global__ void k_union_seg(int64_t n, const State *__restrict__ st, const SegSt
     if (i64 >= n)
         return;
     const int i = (int)i64;
-    const unsigned long long *keys = (st->n_active & 1) ? k1 : k0;
-    const SegState &g = seg[seg_of_key(keys[i], st->shift)];
+    const SegState &g = seg[seg_of_key(sorted_key(st, k0, k1, i), st->shift)];
     const Tree T{nodes, leaf_first, st->n_leaves};
     if (g.minpts <= 2)
         union_query<true, STATS>(i, g.e2, T, spts, leaf_of, parent, core, dev_status, stats);
@@ -201,10 +200,8 @@ __global__ void k_count(int64_t n, const State *__restrict__ st, const SegState 
     if (core[i])
         return;  // member of a dense cell
     int s = 0;
-    if (SEG) {
-        const unsigned long long *keys = (st->n_active & 1) ? k1 : k0;
-        s = seg_of_key(keys[i], st->shift);
-    }
+    if (SEG)
+        s = seg_of_key(sorted_key(st, k0, k1, i), st->shift);
     const SegState &g = seg[s];
     const int minpts = g.minpts;
     if (SEG && minpts <= 2)
@@ -259,10 +256,8 @@ __global__ void k_border(int64_t n, const State *__restrict__ st, const SegState
     if (core[i])
         return;
     int s = 0;
-    if (SEG) {
-        const unsigned long long *keys = (st->n_active & 1) ? k1 : k0;
-        s = seg_of_key(keys[i], st->shift);
-    }
+    if (SEG)
+        s = seg_of_key(sorted_key(st, k0, k1, i), st->shift);
     const SegState &g = seg[s];
     if (SEG && g.minpts <= 2)
         return;  // friends-of-friends: no border points
@@ -327,10 +322,8 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t n, const State *__rest
         return;
     const int i = (int)i64;
     int s = 0;
-    if (SEG) {
-        const unsigned long long *keys = (st->n_active & 1) ? k1 : k0;
-        s = seg_of_key(keys[i], st->shift);
-    }
+    if (SEG)
+        s = seg_of_key(sorted_key(st, k0, k1, i), st->shift);
     const bool fof = seg[s].minpts <= 2;
     int lab = -1;
     if (core[i]) {

@@ -14,6 +14,11 @@
 
 namespace abx {
 
+using u32 = unsigned;
+// Below this size the 32-bit key kernels are not launched (their launch costs
+// more than the lighter passes save).
+constexpr int64_t KEY32_MIN_POINTS = 1 << 16;
+
 // ---- segments and bounds -----------------------------------------------------------
 
 __device__ __forceinline__ void seg_reset(SegState &g, float eps, int minpts)
@@ -33,7 +38,7 @@ __device__ __forceinline__ void seg_reset(SegState &g, float eps, int minpts)
 }
 
 // A single clustering call: one segment covering all n points.
-__global__ void k_init_single(State *st, SegState *seg, int *off, int64_t n, float eps, int minpts)
+__global__ void k_init_single(State *st, SegState *seg, int *off, int64_t n, float eps, int minpts, int allow32)
 {
     if (threadIdx.x == 0) {
         seg_reset(seg[0], eps, minpts);
@@ -41,17 +46,20 @@ __global__ void k_init_single(State *st, SegState *seg, int *off, int64_t n, flo
         off[1] = (int)n;
         st->nseg = 1;
         st->seg_bits = 0;
+        st->allow32 = allow32;
     }
 }
 
 // A batch: segment k gets eps[k], minpts[k] (device copies of the host arrays).
-__global__ void k_init_batch(State *st, SegState *seg, int nseg, const float *eps, const int *minpts, int seg_bits)
+__global__ void k_init_batch(State *st, SegState *seg, int nseg, const float *eps, const int *minpts, int seg_bits,
+                             int allow32)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x)
         seg_reset(seg[k], eps[k], minpts[k]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->nseg = nseg;
         st->seg_bits = seg_bits;
+        st->allow32 = allow32;
     }
 }
 
@@ -203,11 +211,14 @@ __global__ void __launch_bounds__(256) k_bounds_seg(const float *__restrict__ pt
         atomicOr(dev_status, DEV_NONFINITE);
 }
 
-// One thread per segment: choose the quantisation.  The step is the dense-cell
-// side h (slightly below eps/sqrt(3), so a cell's diagonal is at most eps)
-// divided by 2^sub, as long as the extent spans few enough cells for the
-// per-axis width cap; otherwise extent / (2^cap - 1) and no dense cells.
-__global__ void k_quant(State *st, SegState *seg, int nseg, int dense_on, int sub_bits)
+// One thread per segment: choose the quantisation.  With dense cells on, the
+// step is the dense-cell side h (slightly below eps/sqrt(3), so a cell's
+// diagonal is at most eps) divided by 2^sub, as long as the extent spans few
+// enough cells for the per-axis width cap; otherwise extent / (2^cap - 1) and
+// no dense cells.  With dense cells off the grid only has to resolve the
+// points: about log2(cbrt(n)) + 1 bits per axis (some 8 cells per point), which
+// keeps keys short (fewer, lighter radix passes); the tree is as tight.
+__global__ void k_quant(State *st, SegState *seg, const int *__restrict__ off, int nseg, int dense_on, int sub_bits)
 {
     const int cap = min(21, (64 - st->seg_bits) / 3);
     if (blockIdx.x == 0 && threadIdx.x == 0)
@@ -230,7 +241,17 @@ __global__ void k_quant(State *st, SegState *seg, int nseg, int dense_on, int su
         const float h = eps * 0.57735026f * 0.999f;
         int bits = cap, dense_ok = 0;
         float inv_step = 0.0f;
-        if (h > 1e-30f && isfinite(h) && sub_bits < cap) {
+        if (!dense_on) {
+            const int64_t ns = (int64_t)off[k + 1] - off[k];
+            int b = 1;
+            while (b < cap && (1ll << (3 * b)) < 8 * ns)
+                b++;
+            bits = b;
+            const float is = ext > 0.0f ? (float)((1 << b) - 1) / ext : 0.0f;
+            inv_step = isfinite(is) ? is : 0.0f;
+            if (inv_step == 0.0f)
+                inv_step = 1e-30f;  // one cell: every key equal
+        } else if (h > 1e-30f && isfinite(h) && sub_bits < cap) {
             const float ratio = ext / h;
             if (ratio < (float)((1 << (cap - sub_bits)) - 2)) {
                 int bc = 1;
@@ -246,6 +267,8 @@ __global__ void k_quant(State *st, SegState *seg, int nseg, int dense_on, int su
             float is = ext > 0.0f ? (float)((1 << cap) - 1) / ext : 0.0f;
             inv_step = isfinite(is) ? is : 0.0f;
         }
+        if (inv_step == 1e-30f)
+            inv_step = 0.0f;
         g.inv_step = inv_step;
         g.bits = bits;
         g.dense_ok = dense_ok;
@@ -261,21 +284,28 @@ __global__ void k_quant(State *st, SegState *seg, int nseg, int dense_on, int su
 // key = segment << shift | Morton code (shift = 3 * the widest per-axis width),
 // so segments sort apart and each forms its own subtree.
 
-template <bool SEG>
+// Both key widths are launched; the one that does not match the call's key
+// width (decided here, on the device) returns at once.
+template <bool SEG, typename K>
 __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ pts, int64_t n, State *st,
                                                 const SegState *__restrict__ seg, const int *__restrict__ off,
-                                                unsigned long long *__restrict__ keys, unsigned *dev_status)
+                                                K *__restrict__ keys, unsigned *dev_status)
 {
+    const int nseg = st->nseg;
+    const int shift = 3 * st->max_bits;
+    const int kbits = st->seg_bits + shift;
+    const bool key32 = st->allow32 && kbits <= 32;
+    if (key32 != (sizeof(K) == 4))
+        return;
     bool bad = false;
     __shared__ unsigned sh[MAX_PASSES * RADIX];
     for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x)
         sh[i] = 0;
-    const int nseg = st->nseg;
-    const int shift = 3 * st->max_bits;
-    const int np = (st->seg_bits + shift + RADIX_BITS - 1) / RADIX_BITS;
+    const int np = (kbits + RADIX_BITS - 1) / RADIX_BITS;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->shift = shift;
         st->n_passes = np;
+        st->key32 = key32;
     }
     float lx = seg[0].lo[0], ly = seg[0].lo[1], lz = seg[0].lo[2], is = seg[0].inv_step;
     float qmax = (float)((1u << seg[0].bits) - 1u);
@@ -297,7 +327,7 @@ __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ pts, i
         unsigned qy = ty < qmax ? (unsigned)fmaxf(ty, 0.0f) : (unsigned)qmax;
         unsigned qz = tz < qmax ? (unsigned)fmaxf(tz, 0.0f) : (unsigned)qmax;
         unsigned long long key = top | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-        keys[i] = key;
+        keys[i] = (K)key;
         for (int p = 0; p < np; p++)
             atomicAdd(&sh[p * RADIX + (unsigned)((key >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
     }
@@ -348,59 +378,28 @@ __global__ void k_sort_plan(State *st, int64_t n)
 // bounded spins) and scatters through shared memory so that keys of one digit
 // leave as contiguous runs.
 
-constexpr unsigned long long LB_AGG = 1ull << 62;
-constexpr unsigned long long LB_PRE = 2ull << 62;
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Sum the look-back words of tiles [0, tile) for one slot; bounded.
-__device__ unsigned long long lookback_sum(const unsigned long long *lb, int tile, int stride, int slot,
-                                           unsigned *dev_status)
-{
-    unsigned long long excl = 0;
-    for (int t = tile - 1; t >= 0; t--) {
-        unsigned long long v;
-        int spins = 0;
-        while (true) {
-            v = ld_relaxed_u64(lb + (size_t)t * stride + slot);
-            if ((v >> 62) != 0)
-                break;
-            if (++spins > SPIN_LIMIT) {
-                atomicOr(dev_status, DEV_TIMEOUT);
-                return excl;
-            }
-            if (spins > 64)
-                __nanosleep(64);
-        }
-        excl += v & ((1ull << 62) - 1);
-        if ((v >> 62) == 2)
-            break;
-    }
-    return excl;
-}
+constexpr unsigned long long LB_AGG = LB_FLAG_AGG;
+constexpr unsigned long long LB_PRE = LB_FLAG_PRE;
 
 constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr size_t ONESWEEP_SMEM =
-    SORT_TILE * sizeof(unsigned long long) + SORT_TILE * sizeof(unsigned) + SORT_WARPS * RADIX * 4 + 2 * RADIX * 4;
-
-__global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, unsigned long long *k0, unsigned long long *k1,
-                                                              unsigned *v0, unsigned *v1, int64_t n, State *st,
-                                                              unsigned long long *lb_all, unsigned *dev_status)
+template <typename K>
+constexpr size_t onesweep_smem()
 {
+    return SORT_TILE * sizeof(K) + SORT_TILE * sizeof(unsigned) + SORT_WARPS * RADIX * 4 + 2 * RADIX * 4;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, K *k0, K *k1, unsigned *v0, unsigned *v1,
+                                                              int64_t n, State *st, unsigned long long *lb_all,
+                                                              unsigned *dev_status)
+{
+    if (st->key32 != (sizeof(K) == 4))
+        return;
     const int ord = st->pass_ord[pass];
     if (ord < 0)
         return;
-    const unsigned long long *ksrc = (ord & 1) ? k1 : k0;
-    unsigned long long *kdst = (ord & 1) ? k0 : k1;
+    const K *ksrc = (ord & 1) ? k1 : k0;
+    K *kdst = (ord & 1) ? k0 : k1;
     const unsigned *vsrc = (ord & 1) ? v1 : v0;
     unsigned *vdst = (ord & 1) ? v0 : v1;
     const bool first = ord == 0;
@@ -409,7 +408,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, unsigned
     unsigned long long *lb = lb_all + (size_t)pass * ntiles * RADIX;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long *s_keys = reinterpret_cast<unsigned long long *>(smem);
+    K *s_keys = reinterpret_cast<K *>(smem);
     unsigned *s_vals = reinterpret_cast<unsigned *>(s_keys + SORT_TILE);
     unsigned *s_whist = s_vals + SORT_TILE;      // [warps][RADIX]
     unsigned *s_loc = s_whist + SORT_WARPS * RADIX;  // tile-local digit offsets
@@ -426,13 +425,13 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, unsigned
     const int tile = s_tile;
     const int64_t base = (int64_t)tile * SORT_TILE + (int64_t)warp * 32 * SORT_ITEMS + lane;
 
-    unsigned long long key[SORT_ITEMS];
+    K key[SORT_ITEMS];
     unsigned val[SORT_ITEMS];
     unsigned rank[SORT_ITEMS];
 #pragma unroll
     for (int k = 0; k < SORT_ITEMS; k++) {
         const int64_t pos = base + k * 32;
-        key[k] = pos < n ? ksrc[pos] : ~0ull;  // pads rank last in digit RADIX-1 and land at >= n
+        key[k] = pos < n ? ksrc[pos] : (K)~(K)0;  // pads rank last in digit RADIX-1 and land at >= n
     }
 #pragma unroll
     for (int k = 0; k < SORT_ITEMS; k++) {
@@ -469,11 +468,11 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, unsigned
         }
         // publish, then look back
         if (tile == 0) {
-            st_relaxed_u64(lb + d, LB_PRE | cnt);
+            lb_store(lb + d, LB_PRE | cnt);
         } else {
-            st_relaxed_u64(lb + (size_t)tile * RADIX + d, LB_AGG | cnt);
-            excl = lookback_sum(lb, tile, RADIX, d, dev_status);
-            st_relaxed_u64(lb + (size_t)tile * RADIX + d, LB_PRE | (excl + cnt));
+            lb_store(lb + (size_t)tile * RADIX + d, LB_AGG | cnt);
+            excl = lookback<8>(lb, tile, RADIX, tid, dev_status);
+            lb_store(lb + (size_t)tile * RADIX + d, LB_PRE | (excl + cnt));
         }
     }
     // exclusive scan of cnt over digits (tile-local offsets)
@@ -507,7 +506,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, unsigned
     __syncthreads();
 #pragma unroll 4
     for (int i = tid; i < SORT_TILE; i += SORT_THREADS) {
-        const unsigned long long kk = s_keys[i];
+        const K kk = s_keys[i];
         const unsigned dd = (unsigned)(kk >> shift) & (RADIX - 1);
         const unsigned dest = s_glob[dd] + (unsigned)i;
         if ((int64_t)dest < n) {
@@ -524,14 +523,13 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, unsigned
 
 template <bool SEG>
 __global__ void __launch_bounds__(256) k_gather(const float *__restrict__ pts, int64_t n, const State *st,
-                                                const SegState *__restrict__ seg, const unsigned long long *k0,
-                                                const unsigned long long *k1, const unsigned *v0, const unsigned *v1,
+                                                const SegState *__restrict__ seg, const void *k0,
+                                                const void *k1, const unsigned *v0, const unsigned *v1,
                                                 float4 *spts, int *parent, unsigned char *core, int *bmin,
                                                 unsigned *dev_status)
 {
     const int na = st->n_active;
     const unsigned *perm = na == 0 ? nullptr : ((na & 1) ? v1 : v0);
-    const unsigned long long *keys = (na & 1) ? k1 : k0;
     const int shift = st->shift;
     unsigned char c0 = seg[0].minpts <= 1 ? 1 : 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -544,7 +542,7 @@ __global__ void __launch_bounds__(256) k_gather(const float *__restrict__ pts, i
         spts[k] = make_float4(x, y, z, __int_as_float((int)o));
         parent[k] = (int)k;
         if (SEG)
-            c0 = seg[seg_of_key(keys[k], shift)].minpts <= 1 ? 1 : 0;
+            c0 = seg[seg_of_key(sorted_key(st, k0, k1, k), shift)].minpts <= 1 ? 1 : 0;
         core[k] = c0;
         if (bmin)
             bmin[k] = 0x7fffffff;
@@ -565,14 +563,15 @@ static int grid_for(const Work &w, int64_t n, int block, int per_sm = 8)
 void stage_segments_single(const Work &w, float eps, int minpts, cudaStream_t s)
 {
     cudaMemsetAsync(w.st, 0, sizeof(State), s);
-    k_init_single<<<1, 32, 0, s>>>(w.st, w.seg, w.seg_off, w.n, eps, minpts);
+    k_init_single<<<1, 32, 0, s>>>(w.st, w.seg, w.seg_off, w.n, eps, minpts, w.n >= KEY32_MIN_POINTS);
     note_launch();
 }
 
 void stage_segments_batch(const Work &w, const float *eps_dev, const int *minpts_dev, int seg_bits, cudaStream_t s)
 {
     cudaMemsetAsync(w.st, 0, sizeof(State), s);
-    k_init_batch<<<div_up(w.nseg, 128), 128, 0, s>>>(w.st, w.seg, w.nseg, eps_dev, minpts_dev, seg_bits);
+    k_init_batch<<<div_up(w.nseg, 128), 128, 0, s>>>(w.st, w.seg, w.nseg, eps_dev, minpts_dev, seg_bits,
+                                                      w.n >= KEY32_MIN_POINTS);
     note_launch();
 }
 
@@ -589,29 +588,44 @@ void stage_bounds_quant(const Work &w, const float *points, const Params &p, cud
     } else {
         k_bounds_seg<<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.seg, w.seg_off, w.nseg, w.dev_status);
     }
-    k_quant<<<div_up(w.nseg, 128), 128, 0, s>>>(w.st, w.seg, w.nseg, p.dense, p.sub_bits);
+    k_quant<<<div_up(w.nseg, 128), 128, 0, s>>>(w.st, w.seg, w.seg_off, w.nseg, p.dense, p.sub_bits);
     note_launch(2);
     prof_mark(ST_BOUNDS, s);
 }
 
 void stage_morton_sort(const Work &w, const float *points, cudaStream_t s)
 {
-    if (w.nseg == 1)
-        k_morton<false><<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0],
-                                                              w.dev_status);
-    else
-        k_morton<true><<<grid_for(w, w.n, 256), 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0],
-                                                             w.dev_status);
-    note_launch();
+    using u64 = unsigned long long;
+    u32 *k32[2] = {reinterpret_cast<u32 *>(w.keys[0]), reinterpret_cast<u32 *>(w.keys[1])};
+    const bool try32 = w.n >= KEY32_MIN_POINTS;  // must match the allow32 given to the init kernel
+    const int g = grid_for(w, w.n, 256);
+    if (w.nseg == 1) {
+        k_morton<false, u64><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0], w.dev_status);
+        if (try32)
+            k_morton<false, u32><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, k32[0], w.dev_status);
+    } else {
+        k_morton<true, u64><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0], w.dev_status);
+        if (try32)
+            k_morton<true, u32><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, k32[0], w.dev_status);
+    }
+    note_launch(try32 ? 2 : 1);
     prof_mark(ST_MORTON, s);
     k_sort_plan<<<1, RADIX, 0, s>>>(w.st, w.n);
     note_launch();
     cudaMemsetAsync(w.sort_lb, 0, (size_t)MAX_PASSES * w.sort_tiles * RADIX * sizeof(unsigned long long), s);
     const int tiles = div_up(w.n, SORT_TILE);
     for (int pass = 0; pass < MAX_PASSES; pass++)
-        k_onesweep<<<tiles, SORT_THREADS, ONESWEEP_SMEM, s>>>(pass, w.keys[0], w.keys[1], w.vals[0], w.vals[1],
-                                                              w.n, w.st, w.sort_lb, w.dev_status);
+        k_onesweep<u64><<<tiles, SORT_THREADS, onesweep_smem<u64>(), s>>>(pass, w.keys[0], w.keys[1], w.vals[0],
+                                                                          w.vals[1], w.n, w.st, w.sort_lb,
+                                                                          w.dev_status);
     note_launch(MAX_PASSES);
+    if (try32) {
+        for (int pass = 0; pass < 4; pass++)
+            k_onesweep<u32><<<tiles, SORT_THREADS, onesweep_smem<u32>(), s>>>(pass, k32[0], k32[1], w.vals[0],
+                                                                              w.vals[1], w.n, w.st, w.sort_lb,
+                                                                              w.dev_status);
+        note_launch(4);
+    }
     prof_mark(ST_SORT, s);
 }
 
@@ -632,7 +646,9 @@ void stage_gather(const Work &w, const float *points, cudaStream_t s)
 
 void kernels_init_device()
 {
-    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ONESWEEP_SMEM);
+    cudaFuncSetAttribute(k_onesweep<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)onesweep_smem<unsigned long long>());
+    cudaFuncSetAttribute(k_onesweep<u32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<u32>());
 }
 
 }  // namespace abx

@@ -25,14 +25,6 @@
 
 namespace abx {
 
-__device__ __forceinline__ int final_pass_count(const State *st) { return st->n_active; }
-
-__device__ __forceinline__ const unsigned long long *sorted_keys(const State *st, unsigned long long *const k0,
-                                                                  unsigned long long *const k1)
-{
-    return (final_pass_count(st) & 1) ? k1 : k0;
-}
-
 // Leaves are whole subtrees of the point-level radix tree (the tree the
 // build would make with one point per leaf): for a point outside dense cells
 // its leaf is the highest subtree containing it that holds at most leaf_size
@@ -75,9 +67,8 @@ struct LeafFlag {
         if (k == 0)
             return true;
         if (st->nseg > 1) {  // leaves never cross segments
-            const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
-                                                         const_cast<unsigned long long *>(k1));
-            if (seg_of_key(keys[k], st->shift) != seg_of_key(keys[k - 1], st->shift))
+            if (seg_of_key(sorted_key(st, k0, k1, k), st->shift) !=
+                seg_of_key(sorted_key(st, k0, k1, k - 1), st->shift))
                 return true;
         }
         const int x = k - 1, B = leaf_size, last = (int)n - 1;
@@ -114,13 +105,11 @@ __global__ void __launch_bounds__(256) k_dense_cells(int64_t n, State *st, const
 {
     if (!st->dense_ok)
         return;
-    const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
-                                                 const_cast<unsigned long long *>(k1));
     const int sh = 3 * st->sub, shift = st->shift;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long key = keys[k];
+        const unsigned long long key = sorted_key(st, k0, k1, k);
         const unsigned long long c = key >> sh;
-        if (k > 0 && (keys[k - 1] >> sh) == c)
+        if (k > 0 && (sorted_key(st, k0, k1, k - 1) >> sh) == c)
             continue;  // not the first point of its cell
         const SegState &g = seg[seg_of_key(key, shift)];
         if (!g.dense_ok)
@@ -128,11 +117,11 @@ __global__ void __launch_bounds__(256) k_dense_cells(int64_t n, State *st, const
         const float e2 = g.e2;
         const int min_count = max(max(g.minpts, 2), dense_min);
         int64_t e = k + 1;
-        while (e < n && (keys[e] >> sh) == c && e - k < min_count)
+        while (e < n && (sorted_key(st, k0, k1, e) >> sh) == c && e - k < min_count)
             e++;
         if (e - k < min_count)
             continue;
-        while (e < n && (keys[e] >> sh) == c)
+        while (e < n && (sorted_key(st, k0, k1, e) >> sh) == c)
             e++;
         float4 p = spts[k];
         float lx = p.x, ly = p.y, lz = p.z, hx = p.x, hy = p.y, hz = p.z;
@@ -171,10 +160,8 @@ __device__ __forceinline__ unsigned char split_level(unsigned long long a, unsig
 __global__ void __launch_bounds__(256) k_pdelta(int64_t n, const State *st, const unsigned long long *k0,
                                                 const unsigned long long *k1, unsigned char *pdelta)
 {
-    const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
-                                                 const_cast<unsigned long long *>(k1));
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n - 1; k += (int64_t)gridDim.x * blockDim.x)
-        pdelta[k] = split_level(keys[k], keys[k + 1], (int)k);
+        pdelta[k] = split_level(sorted_key(st, k0, k1, k), sorted_key(st, k0, k1, k + 1), (int)k);
 }
 
 __global__ void __launch_bounds__(256) k_leaves(const State *st, SegState *seg, const unsigned long long *k0,
@@ -187,8 +174,6 @@ __global__ void __launch_bounds__(256) k_leaves(const State *st, SegState *seg, 
     const int dense_ok = st->dense_ok;
     const int nseg = st->nseg, shift = st->shift;
     const int64_t n = leaf_first[L];
-    const unsigned long long *keys = sorted_keys(st, const_cast<unsigned long long *>(k0),
-                                                 const_cast<unsigned long long *>(k1));
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L; t += gridDim.x * blockDim.x) {
         int s = leaf_first[t], e = leaf_first[t + 1];
         float4 p = spts[s];
@@ -208,9 +193,9 @@ __global__ void __launch_bounds__(256) k_leaves(const State *st, SegState *seg, 
             delta[t] = pdelta[e - 1];  // the point-level split level at the leaf boundary
         int sg = 0;
         if (nseg > 1) {
-            sg = seg_of_key(keys[s], shift);
-            const bool first = s == 0 || seg_of_key(keys[s - 1], shift) != sg;
-            const bool last = e == n || seg_of_key(keys[e], shift) != sg;
+            sg = seg_of_key(sorted_key(st, k0, k1, s), shift);
+            const bool first = s == 0 || seg_of_key(sorted_key(st, k0, k1, s - 1), shift) != sg;
+            const bool last = e == n || seg_of_key(sorted_key(st, k0, k1, e), shift) != sg;
             if (first && last)
                 seg[sg].root = L - 1 + t;  // a segment of a single leaf
         } else if (L == 1) {

@@ -9,20 +9,6 @@ namespace abx {
 // ids[k] = number of flagged positions <= k, minus one; first[id] = k for each
 // flagged k; first[total] = n; *total_out = total.
 
-constexpr unsigned long long SLB_AGG = 1ull << 62;
-constexpr unsigned long long SLB_PRE = 2ull << 62;
-
-__device__ __forceinline__ unsigned long long sld(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void sst(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 template <class F>
 __global__ void __launch_bounds__(SCAN_THREADS) k_flag_scan(int64_t n, F f, int *ids, int *first, int *total_out,
                                                             unsigned *tile_ctr, unsigned long long *lb,
@@ -66,29 +52,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_flag_scan(int64_t n, F f, int 
     if (tid == 0) {
         unsigned long long excl = 0;
         if (tile == 0) {
-            sst(lb, SLB_PRE | total);
+            lb_store(lb, LB_FLAG_PRE | total);
         } else {
-            sst(lb + tile, SLB_AGG | total);
-            for (int t = tile - 1; t >= 0; t--) {
-                unsigned long long v;
-                int spins = 0;
-                while (true) {
-                    v = sld(lb + t);
-                    if ((v >> 62) != 0)
-                        break;
-                    if (++spins > SPIN_LIMIT) {
-                        atomicOr(dev_status, DEV_TIMEOUT);
-                        v = SLB_PRE;
-                        break;
-                    }
-                    if (spins > 64)
-                        __nanosleep(64);
-                }
-                excl += v & ((1ull << 62) - 1);
-                if ((v >> 62) == 2)
-                    break;
-            }
-            sst(lb + tile, SLB_PRE | (excl + total));
+            lb_store(lb + tile, LB_FLAG_AGG | total);
+            excl = lookback<16>(lb, tile, 1, 0, dev_status);
+            lb_store(lb + tile, LB_FLAG_PRE | (excl + total));
         }
         s_excl = excl;
     }

@@ -337,3 +337,23 @@ def test_pair_histogram_matches_oracle(abx):
     got = h.pair_histogram(edges).cpu().numpy()
     h.close()
     assert np.array_equal(got, oracle.pair_histogram(p, edges))
+
+
+@pytest.mark.parametrize("kw", [dict(dense_cells=-1), dict(dense_cells=-1, leaf_size=8), dict()],
+                         ids=["dense-off", "dense-off-leaf8", "default"])
+@pytest.mark.parametrize("minpts", [2, 6])
+def test_key_widths(abx, kw, minpts):
+    """Inputs large enough for the 32-bit key path: with dense cells off the grid
+    resolves the point density (32-bit keys); with a coarse eps-relative grid
+    the keys fit 32 bits too; otherwise 64-bit keys.  Labels never change."""
+    for n, eps in [(150_000, 0.004), (200_000, 0.02)]:
+        p = clumps(n, 100, n + minpts, a0=0.02)
+        t = torch.from_numpy(p).cuda()
+        abx.profile_enable(True)
+        try:
+            lab = abx.dbscan(t, eps, minpts, params=abx.Params(**kw)).cpu().numpy()
+            bits = abx.profile_counters()["key_bits"]
+        finally:
+            abx.profile_enable(False)
+        assert bits in (32, 64)
+        assert_same(lab, oracle.dbscan(p, eps, minpts), f"{kw} n={n} key bits {bits}")
