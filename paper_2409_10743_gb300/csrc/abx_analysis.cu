@@ -212,7 +212,7 @@ abx_status abx_cluster_stats(const float *points, const int32_t *labels, int64_t
     cudaMemsetAsync(lb, 0, scan_tiles * sizeof(unsigned long long), s);
     const int g = (int)std::min<int64_t>(div_up(n, 256), (int64_t)n_sms * 8);
     k_cs_accumulate<<<g, 256, 0, s>>>(points, labels, n, cnt, sum, status);
-    k_flag_scan<<<(int)scan_tiles, SCAN_THREADS, 0, s>>>(n, ClusterFlag{cnt}, slot, first, &st->n_cells,
+    k_flag_scan<<<(int)scan_tiles, SCAN_THREADS, 0, s>>>(n, FlagItems<ClusterFlag>{{cnt}}, slot, first, &st->n_cells,
                                                          &st->tile_ctr[0], lb, status, st, 0);
     k_cs_centres<<<g, 256, 0, s>>>(st, first, cnt, sum, ids, sizes, centres, rad2);
     k_cs_radius<<<g, 256, 0, s>>>(points, labels, n, slot, centres, rad2);

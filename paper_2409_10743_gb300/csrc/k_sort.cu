@@ -10,6 +10,8 @@
 // bits as the extent needs (fewer radix passes).  When the extent spans more
 // than 2^(21-sub) cells the step falls back to extent / (2^21 - 1).
 // Labels never depend on these choices: they only shape the tree.
+#include <algorithm>
+
 #include "work.cuh"
 
 namespace abx {
@@ -417,102 +419,109 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, K *k0, K
     __shared__ unsigned s_wsum[RADIX / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0)
-        s_tile = (int)atomicAdd(&st->tile_ctr[pass], 1u);
-    for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS)
-        s_whist[i] = 0;
-    __syncthreads();
-    const int tile = s_tile;
-    const int64_t base = (int64_t)tile * SORT_TILE + (int64_t)warp * 32 * SORT_ITEMS + lane;
+    // persistent: each block takes tiles in ticket order until none are left
+    // (a tile only waits on tiles whose blocks are already working on them)
+    while (true) {
+        if (tid == 0)
+            s_tile = (int)atomicAdd(&st->tile_ctr[pass], 1u);
+        for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS)
+            s_whist[i] = 0;
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= ntiles)
+            break;
+        const int64_t base = (int64_t)tile * SORT_TILE + (int64_t)warp * 32 * SORT_ITEMS + lane;
 
-    K key[SORT_ITEMS];
-    unsigned val[SORT_ITEMS];
-    unsigned rank[SORT_ITEMS];
-#pragma unroll
-    for (int k = 0; k < SORT_ITEMS; k++) {
-        const int64_t pos = base + k * 32;
-        key[k] = pos < n ? ksrc[pos] : (K)~(K)0;  // pads rank last in digit RADIX-1 and land at >= n
-    }
-#pragma unroll
-    for (int k = 0; k < SORT_ITEMS; k++) {
-        const int64_t pos = base + k * 32;
-        val[k] = pos < n ? (first ? (unsigned)pos : vsrc[pos]) : 0u;
-    }
-    // stable rank within the warp: lanes with equal digit, in lane order, after
-    // the earlier items of this warp
-    unsigned *wh = s_whist + warp * RADIX;
-    const unsigned lt_mask = (1u << lane) - 1u;
-#pragma unroll
-    for (int k = 0; k < SORT_ITEMS; k++) {
-        const unsigned d = (unsigned)(key[k] >> shift) & (RADIX - 1);
-        const unsigned peers = __match_any_sync(~0u, d);
-        const int leader = __ffs(peers) - 1;
-        unsigned prev = 0;
-        if (lane == leader)
-            prev = atomicAdd(wh + d, (unsigned)__popc(peers));
-        prev = __shfl_sync(~0u, prev, leader);
-        rank[k] = prev + __popc(peers & lt_mask);
-    }
-    __syncthreads();
+        K key[SORT_ITEMS];
+        unsigned val[SORT_ITEMS];
+        unsigned rank[SORT_ITEMS];
+    #pragma unroll
+        for (int k = 0; k < SORT_ITEMS; k++) {
+            const int64_t pos = base + k * 32;
+            key[k] = pos < n ? ksrc[pos] : (K)~(K)0;  // pads rank last in digit RADIX-1 and land at >= n
+        }
+    #pragma unroll
+        for (int k = 0; k < SORT_ITEMS; k++) {
+            const int64_t pos = base + k * 32;
+            val[k] = pos < n ? (first ? (unsigned)pos : vsrc[pos]) : 0u;
+        }
+        // stable rank within the warp: lanes with equal digit, in lane order, after
+        // the earlier items of this warp
+        unsigned *wh = s_whist + warp * RADIX;
+        const unsigned lt_mask = (1u << lane) - 1u;
+    #pragma unroll
+        for (int k = 0; k < SORT_ITEMS; k++) {
+            const unsigned d = (unsigned)(key[k] >> shift) & (RADIX - 1);
+            const unsigned peers = __match_any_sync(~0u, d);
+            const int leader = __ffs(peers) - 1;
+            unsigned prev = 0;
+            if (lane == leader)
+                prev = atomicAdd(wh + d, (unsigned)__popc(peers));
+            prev = __shfl_sync(~0u, prev, leader);
+            rank[k] = prev + __popc(peers & lt_mask);
+        }
+        __syncthreads();
 
-    // thread d < RADIX: per-warp exclusive offsets and the tile count of digit d
-    unsigned cnt = 0;
-    unsigned long long excl = 0;
-    if (tid < RADIX) {
-        const int d = tid;
-#pragma unroll
-        for (int w = 0; w < SORT_WARPS; w++) {
-            unsigned c = s_whist[w * RADIX + d];
-            s_whist[w * RADIX + d] = cnt;
-            cnt += c;
+        // thread d < RADIX: per-warp exclusive offsets and the tile count of digit d
+        unsigned cnt = 0;
+        unsigned long long excl = 0;
+        if (tid < RADIX) {
+            const int d = tid;
+    #pragma unroll
+            for (int w = 0; w < SORT_WARPS; w++) {
+                unsigned c = s_whist[w * RADIX + d];
+                s_whist[w * RADIX + d] = cnt;
+                cnt += c;
+            }
+            // publish, then look back
+            if (tile == 0) {
+                lb_store(lb + d, LB_PRE | cnt);
+            } else {
+                lb_store(lb + (size_t)tile * RADIX + d, LB_AGG | cnt);
+                excl = lookback<8>(lb, tile, RADIX, tid, dev_status);
+                lb_store(lb + (size_t)tile * RADIX + d, LB_PRE | (excl + cnt));
+            }
         }
-        // publish, then look back
-        if (tile == 0) {
-            lb_store(lb + d, LB_PRE | cnt);
-        } else {
-            lb_store(lb + (size_t)tile * RADIX + d, LB_AGG | cnt);
-            excl = lookback<8>(lb, tile, RADIX, tid, dev_status);
-            lb_store(lb + (size_t)tile * RADIX + d, LB_PRE | (excl + cnt));
+        // exclusive scan of cnt over digits (tile-local offsets)
+        unsigned x = cnt;
+    #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(~0u, x, o);
+            if (lane >= o)
+                x += y;
         }
-    }
-    // exclusive scan of cnt over digits (tile-local offsets)
-    unsigned x = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(~0u, x, o);
-        if (lane >= o)
-            x += y;
-    }
-    if (tid < RADIX && lane == 31)
-        s_wsum[warp] = x;
-    __syncthreads();
-    if (tid < RADIX) {
-        unsigned wpre = 0;
-        for (int w = 0; w < warp; w++)
-            wpre += s_wsum[w];
-        const unsigned loc = wpre + x - cnt;
-        s_loc[tid] = loc;
-        s_glob[tid] = st->hist[pass][tid] + (unsigned)excl - loc;
-    }
-    __syncthreads();
+        if (tid < RADIX && lane == 31)
+            s_wsum[warp] = x;
+        __syncthreads();
+        if (tid < RADIX) {
+            unsigned wpre = 0;
+            for (int w = 0; w < warp; w++)
+                wpre += s_wsum[w];
+            const unsigned loc = wpre + x - cnt;
+            s_loc[tid] = loc;
+            s_glob[tid] = st->hist[pass][tid] + (unsigned)excl - loc;
+        }
+        __syncthreads();
 
-#pragma unroll
-    for (int k = 0; k < SORT_ITEMS; k++) {
-        const unsigned dd = (unsigned)(key[k] >> shift) & (RADIX - 1);
-        const unsigned lp = s_loc[dd] + s_whist[warp * RADIX + dd] + rank[k];
-        s_keys[lp] = key[k];
-        s_vals[lp] = val[k];
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int i = tid; i < SORT_TILE; i += SORT_THREADS) {
-        const K kk = s_keys[i];
-        const unsigned dd = (unsigned)(kk >> shift) & (RADIX - 1);
-        const unsigned dest = s_glob[dd] + (unsigned)i;
-        if ((int64_t)dest < n) {
-            kdst[dest] = kk;
-            vdst[dest] = s_vals[i];
+    #pragma unroll
+        for (int k = 0; k < SORT_ITEMS; k++) {
+            const unsigned dd = (unsigned)(key[k] >> shift) & (RADIX - 1);
+            const unsigned lp = s_loc[dd] + s_whist[warp * RADIX + dd] + rank[k];
+            s_keys[lp] = key[k];
+            s_vals[lp] = val[k];
         }
+        __syncthreads();
+    #pragma unroll 4
+        for (int i = tid; i < SORT_TILE; i += SORT_THREADS) {
+            const K kk = s_keys[i];
+            const unsigned dd = (unsigned)(kk >> shift) & (RADIX - 1);
+            const unsigned dest = s_glob[dd] + (unsigned)i;
+            if ((int64_t)dest < n) {
+                kdst[dest] = kk;
+                vdst[dest] = s_vals[i];
+            }
+        }
+        __syncthreads();  // the next tile reuses the shared buffers
     }
 }
 
@@ -613,7 +622,7 @@ void stage_morton_sort(const Work &w, const float *points, cudaStream_t s)
     k_sort_plan<<<1, RADIX, 0, s>>>(w.st, w.n);
     note_launch();
     cudaMemsetAsync(w.sort_lb, 0, (size_t)MAX_PASSES * w.sort_tiles * RADIX * sizeof(unsigned long long), s);
-    const int tiles = div_up(w.n, SORT_TILE);
+    const int tiles = (int)std::min<int64_t>(div_up(w.n, SORT_TILE), 2 * (int64_t)w.n_sms);
     for (int pass = 0; pass < MAX_PASSES; pass++)
         k_onesweep<u64><<<tiles, SORT_THREADS, onesweep_smem<u64>(), s>>>(pass, w.keys[0], w.keys[1], w.vals[0],
                                                                           w.vals[1], w.n, w.st, w.sort_lb,

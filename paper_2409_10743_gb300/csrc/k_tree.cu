@@ -91,6 +91,77 @@ struct LeafFlag {
                     return true;
         return false;
     }
+
+    // The SCAN_ITEMS flags starting at base (a multiple of 16).  For leaf sizes
+    // up to 8 and no dense cells or segments the rule needs only the split
+    // levels within 8 boundaries of each boundary: they are loaded once into a
+    // register window and compared four at a time.
+    __device__ unsigned flags(int64_t base64, int64_t n64) const
+    {
+        const bool simple = leaf_size <= 8 && !st->dense_ok && st->nseg == 1;
+        unsigned m = 0;
+        if (!simple) {
+#pragma unroll 1
+            for (int j = 0; j < SCAN_ITEMS; j++)
+                if (base64 + j < n64 && (*this)(base64 + j))
+                    m |= 1u << j;
+            return m;
+        }
+        const int base = (int)base64, n = (int)n64, B = leaf_size;
+        // window byte i = split level of boundary base - 12 + i (255 outside 0 .. n-2)
+        unsigned w[10];
+#pragma unroll
+        for (int k = 0; k < 10; k++) {
+            const int y0 = base - 12 + 4 * k;
+            if (y0 >= 0 && y0 + 3 <= n - 2) {
+                w[k] = *reinterpret_cast<const unsigned *>(pdelta + y0);
+            } else {
+                unsigned v = 0;
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    const int y = y0 + t;
+                    const unsigned b = (y >= 0 && y <= n - 2) ? pdelta[y] : 255u;
+                    v |= b << (8 * t);
+                }
+                w[k] = v;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j++) {
+            const int k = base + j;
+            if (k >= n)
+                break;
+            if (k == 0) {
+                m |= 1u;
+                continue;
+            }
+            // boundary x = k - 1 sits at window byte j + 11
+            const int ox = j + 11;
+            const unsigned d = (w[ox / 4] >> (8 * (ox % 4))) & 0xffu;
+            const unsigned dd = d * 0x01010101u;
+            // right: boundaries x+1 .. x+8 at bytes j+12 .. j+19; nearest with level >= d
+            const int orr = j + 12;
+            const unsigned r0 = __funnelshift_r(w[orr / 4], w[orr / 4 + 1], 8 * (orr % 4));
+            const unsigned r1 = __funnelshift_r(w[orr / 4 + 1], w[orr / 4 + 2], 8 * (orr % 4));
+            const unsigned long long mr =
+                (unsigned long long)__vcmpgeu4(r0, dd) | ((unsigned long long)__vcmpgeu4(r1, dd) << 32);
+            // left: boundaries x-8 .. x-1 at bytes j+3 .. j+10; nearest with level > d
+            const int ol = j + 3;
+            const unsigned l0 = __funnelshift_r(w[ol / 4], w[ol / 4 + 1], 8 * (ol % 4));
+            const unsigned l1 = __funnelshift_r(w[ol / 4 + 1], w[ol / 4 + 2], 8 * (ol % 4));
+            const unsigned long long ml =
+                (unsigned long long)__vcmpgtu4(l0, dd) | ((unsigned long long)__vcmpgtu4(l1, dd) << 32);
+            if (!mr || !ml) {
+                m |= 1u << j;  // one side alone holds more than 8 points
+                continue;
+            }
+            const int yr = k + (__ffsll((long long)mr) - 1) / 8;              // x + 1 + byte
+            const int yl = k - 9 + (63 - __clzll((long long)ml)) / 8;          // x - 8 + byte
+            if (yr - yl > B)
+                m |= 1u << j;
+        }
+        return m;
+    }
 };
 
 // ---- dense cells (one pass, no scan) ---------------------------------------------

@@ -9,6 +9,21 @@ namespace abx {
 // ids[k] = number of flagged positions <= k, minus one; first[id] = k for each
 // flagged k; first[total] = n; *total_out = total.
 
+// Flag functors give one position's flag; FlagItems turns that into the
+// SCAN_ITEMS flags of a thread (functors may instead compute them together).
+template <class F>
+struct FlagItems : F {
+    __device__ unsigned flags(int64_t base, int64_t n) const
+    {
+        unsigned m = 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j++)
+            if (base + j < n && (*this)(base + j))
+                m |= 1u << j;
+        return m;
+    }
+};
+
 template <class F>
 __global__ void __launch_bounds__(SCAN_THREADS) k_flag_scan(int64_t n, F f, int *ids, int *first, int *total_out,
                                                             unsigned *tile_ctr, unsigned long long *lb,
@@ -25,13 +40,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_flag_scan(int64_t n, F f, int 
     __syncthreads();
     const int tile = s_tile;
     const int64_t base = (int64_t)tile * SCAN_TILE + (int64_t)tid * SCAN_ITEMS;
-    unsigned flags = 0;  // bit j = flag of item j
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; j++) {
-        int64_t pos = base + j;
-        if (pos < n && f(pos))
-            flags |= 1u << j;
-    }
+    const unsigned flags = f.flags(base, n);  // bit j = flag of item base + j
     unsigned c = __popc(flags);
     unsigned x = c;
 #pragma unroll
