@@ -16,6 +16,7 @@ region), the roofline of the dominant kernel, the oracle's CPU baseline,
 clocks sampled during the timed region and the number of kernels launched.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--config C2] [--params leaf_size=8,dense_cells=-1,block=128]
 
 Under torchrun (N > 1) every rank clusters its own independent instance
 (weak scaling: replicas, no collective on the data path); the timed region is
@@ -330,6 +331,8 @@ def main():
     ap.add_argument("--served-requests", type=int, default=120)
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--params", default="",
+                    help="fixed tuning parameters instead of the autotuner, e.g. leaf_size=8,dense_cells=-1,block=128")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_setup()
@@ -356,7 +359,10 @@ def main():
     stream = torch.cuda.current_stream()
 
     tuned = None
-    if not args.no_autotune:  # part of warm-up: the autotuner's pick is used by every timed step
+    if args.params:  # remembered for this size class: every call below uses them
+        tuned = {k: int(v) for k, v in (kv.split("=") for kv in args.params.split(",") if kv)}
+        abx.tune_set(n, cfg.minpts, tuned)
+    elif not args.no_autotune:  # part of warm-up: the autotuner's pick is used by every timed step
         tuned = abx.autotune(t, cfg.eps, cfg.minpts)
     for _ in range(args.warmup):
         abx.dbscan(t, cfg.eps, cfg.minpts, labels=labels)
@@ -444,7 +450,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg.describe(), "n_points": n, "eps": cfg.eps, "minpts": cfg.minpts,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single instance",
-                       "l2": "no flush: inputs (1.6 GB) and working set exceed the 129 MB L2"},
+                       "l2": f"no flush: inputs ({n * 12 / 1e9:.2f} GB) and working set exceed the 129 MB L2"},
             "e2e": e2e, "roofline": roof, "pipeline": pipeline,
             "stage_ms": {k: round(v, 3) for k, v in mean_ms.items()}, "counters": counters,
             "params": tuned if tuned is not None else "library defaults",
