@@ -212,7 +212,7 @@ abx_status abx_tune_set(int64_t n, int32_t minpts, const abx_params *params);
 /*
  * abx_profile_enable -- on = 1: every clustering call records a CUDA event on
  * its stream at each stage boundary (bounds, morton, sort, gather, cells,
- * leaves, build, count, union, border, finalize).  on = 2: the same, and the
+ * leaves, build, candidates, count, union, border, finalize).  on = 2: the same, and the
  * pair traversal also counts its work (a slower, instrumented kernel; read
  * with abx_profile_traversal).  on = 0: off.  Meant for one call at a time
  * (benchmarks): concurrent profiled calls overwrite each other's events.

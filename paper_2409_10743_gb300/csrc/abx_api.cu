@@ -136,7 +136,7 @@ static void carve(Carver &c, Work &w, int64_t n, int nseg)
     w.seg_eps_in = c.take<float>((size_t)nseg);
     w.seg_minpts_in = c.take<int>((size_t)nseg);
     w.leaf_seg = c.take<int>(N);
-    w.sort_tiles = (size_t)div_up(n, SORT_TILE);
+    w.sort_tiles = (size_t)div_up(n, SORT_TILE_MIN);
     w.scan_tiles = (size_t)div_up(n, SCAN_TILE);
     w.st = c.take<State>(1);
     w.keys[0] = c.take<unsigned long long>(N);
@@ -154,6 +154,8 @@ static void carve(Carver &c, Work &w, int64_t n, int nseg)
     w.nodes = c.take<float4>(2 * (2 * N - 1));
     w.slot = c.take<unsigned long long>(N);
     w.frontier = c.take<int4>(N);
+    w.cand = w.frontier;
+    w.cand2 = reinterpret_cast<int2 *>(w.slot);
     w.right_of = c.take<int>(N);
     w.parent = c.take<int>(N);
     w.core = c.take<unsigned char>(N);
@@ -385,7 +387,7 @@ abx_status abx_device_status(abx_stream stream)
 }
 
 static const char *k_stage_names[ST_NUM] = {"bounds", "morton", "sort", "gather", "cells", "leaves",
-                                           "build", "count", "union", "border", "finalize"};
+                                           "build", "candidates", "count", "union", "border", "finalize"};
 
 abx_status abx_profile_enable(int32_t on)
 {

@@ -19,9 +19,15 @@ constexpr int SENTINEL = -1;        // rope of the right-most path (paper, fig. 
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int MAX_PASSES = 8;       // 64-bit keys, 8 bits per pass
-constexpr int SORT_THREADS = 512;
-constexpr int SORT_ITEMS = 8;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_MIN_BLOCKS = 2;  // blocks per SM the sort pass is compiled for
+// keys per thread of a sort pass: as many as the registers of 2 blocks per SM
+// hold without spilling (key, value and rank per item)
+template <typename K>
+constexpr int sort_items() { return sizeof(K) == 4 ? 32 : 16; }
+template <typename K>
+constexpr int sort_tile() { return SORT_THREADS * sort_items<K>(); }
+constexpr int SORT_TILE_MIN = SORT_THREADS * 16;  // the smaller tile sizes the look-back buffer
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -174,6 +180,20 @@ __device__ __forceinline__ float box_dist2_rn(float px, float py, float pz, floa
     float dx = fmaxf(0.0f, fmaxf(__fsub_rn(lo.x, px), __fsub_rn(px, hi.x)));
     float dy = fmaxf(0.0f, fmaxf(__fsub_rn(lo.y, py), __fsub_rn(py, hi.y)));
     float dz = fmaxf(0.0f, fmaxf(__fsub_rn(lo.z, pz), __fsub_rn(pz, hi.z)));
+    float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    return __fadd_rn(s, __fmul_rn(dz, dz));
+}
+
+// Rounded distance between two boxes, per axis the gap max(0, lo_b - hi_a,
+// lo_a - hi_b).  For p in box a and q in box b, q_x - p_x >= lo_b - hi_a
+// exactly, and rounding is monotone, so |fl(p_x - q_x)| >= fl(gap); squares
+// and sums keep the order: the value is <= dist2_rn(p, q) for every such
+// pair, and pruning at > e2 never drops a neighbour pair.
+__device__ __forceinline__ float box_box_dist2_rn(float4 alo, float4 ahi, float4 blo, float4 bhi)
+{
+    float dx = fmaxf(0.0f, fmaxf(__fsub_rn(blo.x, ahi.x), __fsub_rn(alo.x, bhi.x)));
+    float dy = fmaxf(0.0f, fmaxf(__fsub_rn(blo.y, ahi.y), __fsub_rn(alo.y, bhi.y)));
+    float dz = fmaxf(0.0f, fmaxf(__fsub_rn(blo.z, ahi.z), __fsub_rn(alo.z, bhi.z)));
     float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
     return __fadd_rn(s, __fmul_rn(dz, dz));
 }

@@ -40,6 +40,63 @@ __device__ __forceinline__ bool node_ok(int node, int L, unsigned &steps, unsign
 __device__ __forceinline__ float4 node_lo(const Tree &t, int i) { return __ldg(t.nodes + 2 * (size_t)i); }
 __device__ __forceinline__ float4 node_hi(const Tree &t, int i) { return __ldg(t.nodes + 2 * (size_t)i + 1); }
 
+// ---- candidate leaves --------------------------------------------------------------
+// The pair traversal of a point starts at its leaf's rope and descends into
+// every subtree after its leaf that its own box test cannot rule out.  A node
+// whose rounded distance to the LEAF's box exceeds eps is out of reach of
+// every point of the leaf (box_box_dist2_rn is a lower bound of the point's
+// own box distance), so one traversal per leaf with the leaf's box finds the
+// leaves after it that any of its points can reach: its candidate leaves.
+// Each point then tests only the points of those leaves and visits no node.
+// Up to CAND_K - 1 candidates are kept; when there are more, the last slot
+// holds -(node + 2) for the leaf node where the list ran out, and the points
+// walk the ropes from there on with their own box tests (which visits that
+// leaf and everything after it in pre-order).  -1 ends a list.
+
+constexpr int CAND_K = 6;
+
+template <bool SEG>
+__global__ void k_cand(const State *__restrict__ st, const SegState *__restrict__ seg,
+                       const int *__restrict__ leaf_seg, const float4 *__restrict__ nodes, int4 *cand, int2 *cand2,
+                       unsigned *dev_status)
+{
+    const int L = st->n_leaves;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= L)
+        return;
+    const Tree T{nodes, nullptr, L};
+    const float e2 = seg[SEG ? leaf_seg[a] : 0].e2;
+    const float4 alo = node_lo(T, L - 1 + a), ahi = node_hi(T, L - 1 + a);
+    int out[CAND_K];
+#pragma unroll
+    for (int k = 0; k < CAND_K; k++)
+        out[k] = SENTINEL;
+    int k = 0;
+    int node = __float_as_int(ahi.w);
+    unsigned steps = 0;
+    while (node != SENTINEL) {
+        if (!node_ok(node, L, steps, dev_status))
+            break;
+        const float4 lo = node_lo(T, node), hi = node_hi(T, node);
+        if (box_box_dist2_rn(alo, ahi, lo, hi) <= e2) {
+            if (node < L - 1) {
+                node = __float_as_int(lo.w);
+                continue;
+            }
+            const int v = k == CAND_K - 1 ? -(node + 2) : node - (L - 1);
+    #pragma unroll
+            for (int q = 0; q < CAND_K; q++)
+                if (q == k)
+                    out[q] = v;
+            if (++k == CAND_K)
+                break;
+        }
+        node = __float_as_int(hi.w);
+    }
+    cand[a] = make_int4(out[0], out[1], out[2], out[3]);
+    cand2[a] = make_int2(out[4], out[5]);
+}
+
 // ---- pair traversal with union-find ------------------------------------------------
 // FoF (minPts <= 2): every neighbour pair is merged and both ends become core.
 // DBSCAN (minPts > 2): only core threads run, and only core-core pairs merge.
@@ -54,8 +111,8 @@ struct TravStats {
 template <bool FOF, bool STATS>
 __device__ __forceinline__ void union_query(const int i, const float e2, const Tree &T,
                                             const float4 *__restrict__ spts, const int *__restrict__ leaf_of,
-                                            int *parent, unsigned char *core, unsigned *dev_status,
-                                            TravStats *stats)
+                                            const int4 *__restrict__ cand, const int2 *__restrict__ cand2, int *parent,
+                                            unsigned char *core, unsigned *dev_status, TravStats *stats)
 {
     const int L = T.L;
     const float4 p = spts[i];
@@ -82,7 +139,64 @@ __device__ __forceinline__ void union_query(const int i, const float e2, const T
             }
         }
     }
-    int node = __float_as_int(node_hi(T, my_leaf).w);
+    // the points of leaf [s, e): one of the candidate leaves of i's leaf
+    auto test_leaf = [&](const unsigned lw, const int e) {
+        const int s = (int)(lw & ~DENSE_BIT);
+        if (STATS)
+            c_leaf++;
+        if (lw & DENSE_BIT) {
+            // all points of a dense cell are core and already one set:
+            // one link is enough, none if i is already in that set
+            if (uf_find(parent, i) == uf_find(parent, s)) {
+                found = true;
+                return;
+            }
+            for (int j = s; j < e; j++) {
+                const float4 q = __ldg(spts + j);
+                if (STATS)
+                    c_test++;
+                if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
+                    uf_unite(parent, spts, i, s);
+                    if (STATS)
+                        c_union++;
+                    found = true;
+                    return;
+                }
+            }
+            return;
+        }
+        for (int j = s; j < e; j++) {
+            const float4 q = __ldg(spts + j);
+            if (STATS)
+                c_test++;
+            if ((FOF || core[j]) && dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
+                uf_unite(parent, spts, i, j);
+                if (STATS)
+                    c_union++;
+                if (FOF) {
+                    found = true;
+                    core[j] = 1;
+                }
+            }
+        }
+    };
+    const int me = my_leaf - (L - 1);
+    const int4 c4 = cand[me];
+    const int2 c2 = cand2[me];
+    int resume = SENTINEL;
+    for (int c = 0; c < CAND_K; c++) {
+        const int v = c == 0 ? c4.x : c == 1 ? c4.y : c == 2 ? c4.z : c == 3 ? c4.w : c == 4 ? c2.x : c2.y;
+        if (v == SENTINEL)
+            break;
+        if (v < 0) {
+            resume = -v - 2;
+            break;
+        }
+        test_leaf(__float_as_uint(node_lo(T, L - 1 + v).w), leaf_first[v + 1]);
+    }
+    // more candidates than the list holds: the plain pair traversal from the
+    // leaf where the list ran out
+    int node = resume;
     unsigned steps = 0;
     while (node != SENTINEL) {
         if (!node_ok(node, L, steps, dev_status))
@@ -95,46 +209,7 @@ __device__ __forceinline__ void union_query(const int i, const float e2, const T
                 node = __float_as_int(lo.w);
                 continue;
             }
-            if (STATS)
-                c_leaf++;
-            const unsigned lw = __float_as_uint(lo.w);
-            const int s = (int)(lw & ~DENSE_BIT);
-            const int e = leaf_first[node - (L - 1) + 1];
-            if (lw & DENSE_BIT) {
-                // all points of a dense cell are core and already one set:
-                // one link is enough, none if i is already in that set
-                if (uf_find(parent, i) == uf_find(parent, s)) {
-                    found = true;
-                } else {
-                    for (int j = s; j < e; j++) {
-                        float4 q = __ldg(spts + j);
-                        if (STATS)
-                            c_test++;
-                        if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
-                            uf_unite(parent, spts, i, s);
-                            if (STATS)
-                                c_union++;
-                            found = true;
-                            break;
-                        }
-                    }
-                }
-            } else {
-                for (int j = s; j < e; j++) {
-                    float4 q = __ldg(spts + j);
-                    if (STATS)
-                        c_test++;
-                    if ((FOF || core[j]) && dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
-                        uf_unite(parent, spts, i, j);
-                        if (STATS)
-                            c_union++;
-                        if (FOF) {
-                            found = true;
-                            core[j] = 1;
-                        }
-                    }
-                }
-            }
+            test_leaf(__float_as_uint(lo.w), leaf_first[node - (L - 1) + 1]);
         }
         node = __float_as_int(hi.w);
     }
@@ -150,9 +225,10 @@ __device__ __forceinline__ void union_query(const int i, const float e2, const T
 }
 
 template <bool FOF, bool STATS>
-__global__ void k_union(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
+__global__ void __launch_bounds__(1024, 2) k_union(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
                         const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
-                        const int *__restrict__ leaf_of, const int *__restrict__ leaf_first, int *parent,
+                        const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
+                        const int4 *__restrict__ cand, const int2 *__restrict__ cand2, int *parent,
                         unsigned char *core, unsigned *dev_status, TravStats *stats)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -162,15 +238,16 @@ __global__ void k_union(int64_t n, const State *__restrict__ st, const SegState 
     if (!FOF && !core[i])
         return;
     const Tree T{nodes, leaf_first, st->n_leaves};
-    union_query<FOF, STATS>(i, seg[0].e2, T, spts, leaf_of, parent, core, dev_status, stats);
+    union_query<FOF, STATS>(i, seg[0].e2, T, spts, leaf_of, cand, cand2, parent, core, dev_status, stats);
 }
 
 // Many segments: each query takes its segment's eps and mode from its key.
 template <bool STATS>
-__global__ void k_union_seg(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
+__global__ void __launch_bounds__(1024, 2) k_union_seg(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
                             const unsigned long long *k0, const unsigned long long *k1,
                             const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
-                            const int *__restrict__ leaf_of, const int *__restrict__ leaf_first, int *parent,
+                            const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
+                        const int4 *__restrict__ cand, const int2 *__restrict__ cand2, int *parent,
                             unsigned char *core, unsigned *dev_status, TravStats *stats)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,9 +257,9 @@ __global__ void k_union_seg(int64_t n, const State *__restrict__ st, const SegSt
     const SegState &g = seg[seg_of_key(sorted_key(st, k0, k1, i), st->shift)];
     const Tree T{nodes, leaf_first, st->n_leaves};
     if (g.minpts <= 2)
-        union_query<true, STATS>(i, g.e2, T, spts, leaf_of, parent, core, dev_status, stats);
+        union_query<true, STATS>(i, g.e2, T, spts, leaf_of, cand, cand2, parent, core, dev_status, stats);
     else if (core[i])
-        union_query<false, STATS>(i, g.e2, T, spts, leaf_of, parent, core, dev_status, stats);
+        union_query<false, STATS>(i, g.e2, T, spts, leaf_of, cand, cand2, parent, core, dev_status, stats);
 }
 
 // ---- core counting with early termination (minPts > 2) -------------------------------
@@ -348,14 +425,20 @@ void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t
     const int g = div_up(w.n, B);
     TravStats *stats = (TravStats *)w.stats;
     cudaMemsetAsync(labels, 0xff, (size_t)w.n * sizeof(int32_t), s);  // noise = -1
+    if (w.nseg == 1)
+        k_cand<false><<<div_up(w.n, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.cand, w.cand2, w.dev_status);
+    else
+        k_cand<true><<<div_up(w.n, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.cand, w.cand2, w.dev_status);
+    note_launch();
+    prof_mark(ST_CANDS, s);
     if (w.nseg == 1) {
         if (w.any_fof) {
             if (stats)
                 k_union<true, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                    w.parent, w.core, w.dev_status, stats);
+                                                    w.cand, w.cand2, w.parent, w.core, w.dev_status, stats);
             else
                 k_union<true, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                     w.parent, w.core, w.dev_status, nullptr);
+                                                     w.cand, w.cand2, w.parent, w.core, w.dev_status, nullptr);
             note_launch();
             prof_mark(ST_UNION, s);
         } else {
@@ -365,10 +448,10 @@ void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t
             prof_mark(ST_COUNT, s);
             if (stats)
                 k_union<false, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                     w.parent, w.core, w.dev_status, stats);
+                                                     w.cand, w.cand2, w.parent, w.core, w.dev_status, stats);
             else
                 k_union<false, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                      w.parent, w.core, w.dev_status, nullptr);
+                                                      w.cand, w.cand2, w.parent, w.core, w.dev_status, nullptr);
             note_launch();
             prof_mark(ST_UNION, s);
             k_border<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
@@ -387,10 +470,10 @@ void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t
         }
         if (stats)
             k_union_seg<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_of,
-                                              w.leaf_first, w.parent, w.core, w.dev_status, stats);
+                                              w.leaf_first, w.cand, w.cand2, w.parent, w.core, w.dev_status, stats);
         else
             k_union_seg<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_of,
-                                               w.leaf_first, w.parent, w.core, w.dev_status, nullptr);
+                                               w.leaf_first, w.cand, w.cand2, w.parent, w.core, w.dev_status, nullptr);
         note_launch();
         prof_mark(ST_UNION, s);
         if (w.any_dbscan) {

@@ -373,7 +373,7 @@ __global__ void k_sort_plan(State *st, int64_t n)
 }
 
 // ---- onesweep pass ------------------------------------------------------------------
-// One tile of SORT_TILE keys per block (tile ids handed out in launch order, so
+// One tile of sort_tile<K>() keys per block (tile ids handed out in launch order, so
 // a tile only ever waits on tiles that are already running).  Each warp ranks
 // its keys by digit with __match_any_sync, the tile publishes its digit counts,
 // looks back across earlier tiles for its global prefix (decoupled look-back,
@@ -384,14 +384,15 @@ constexpr unsigned long long LB_AGG = LB_FLAG_AGG;
 constexpr unsigned long long LB_PRE = LB_FLAG_PRE;
 
 constexpr int SORT_WARPS = SORT_THREADS / 32;
+static int g_sort_blocks_per_sm = SORT_MIN_BLOCKS;  // set per process by kernels_init_device
 template <typename K>
 constexpr size_t onesweep_smem()
 {
-    return SORT_TILE * sizeof(K) + SORT_TILE * sizeof(unsigned) + SORT_WARPS * RADIX * 4 + 2 * RADIX * 4;
+    return sort_tile<K>() * (sizeof(K) + sizeof(unsigned)) + SORT_WARPS * RADIX * 4 + 2 * RADIX * 4;
 }
 
 template <typename K>
-__global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, K *k0, K *k1, unsigned *v0, unsigned *v1,
+__global__ void __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) k_onesweep(int pass, K *k0, K *k1, unsigned *v0, unsigned *v1,
                                                               int64_t n, State *st, unsigned long long *lb_all,
                                                               unsigned *dev_status)
 {
@@ -406,7 +407,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, K *k0, K
     unsigned *vdst = (ord & 1) ? v0 : v1;
     const bool first = ord == 0;
     const int shift = pass * RADIX_BITS;
+    constexpr int SORT_ITEMS = sort_items<K>();
+    constexpr int SORT_TILE = sort_tile<K>();
     const int ntiles = div_up(n, SORT_TILE);
+    const unsigned nn = (unsigned)n;
     unsigned long long *lb = lb_all + (size_t)pass * ntiles * RADIX;
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -430,29 +434,37 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, K *k0, K
         const int tile = s_tile;
         if (tile >= ntiles)
             break;
-        const int64_t base = (int64_t)tile * SORT_TILE + (int64_t)warp * 32 * SORT_ITEMS + lane;
+        // positions fit 32 bits: n < 2^31 and a tile ends at most SORT_TILE - 1 past n
+        const unsigned base = (unsigned)tile * SORT_TILE + (unsigned)warp * 32 * SORT_ITEMS + lane;
 
         K key[SORT_ITEMS];
         unsigned val[SORT_ITEMS];
         unsigned rank[SORT_ITEMS];
     #pragma unroll
         for (int k = 0; k < SORT_ITEMS; k++) {
-            const int64_t pos = base + k * 32;
-            key[k] = pos < n ? ksrc[pos] : (K)~(K)0;  // pads rank last in digit RADIX-1 and land at >= n
+            const unsigned pos = base + k * 32;
+            key[k] = pos < nn ? ksrc[pos] : (K)~(K)0;  // pads rank last in digit RADIX-1 and land at >= n
         }
     #pragma unroll
         for (int k = 0; k < SORT_ITEMS; k++) {
-            const int64_t pos = base + k * 32;
-            val[k] = pos < n ? (first ? (unsigned)pos : vsrc[pos]) : 0u;
+            const unsigned pos = base + k * 32;
+            val[k] = pos < nn ? (first ? pos : vsrc[pos]) : 0u;
         }
         // stable rank within the warp: lanes with equal digit, in lane order, after
-        // the earlier items of this warp
+        // the earlier items of this warp.  The lanes sharing a digit are found
+        // with one ballot per digit bit (cheaper than a general match).
         unsigned *wh = s_whist + warp * RADIX;
         const unsigned lt_mask = (1u << lane) - 1u;
     #pragma unroll
         for (int k = 0; k < SORT_ITEMS; k++) {
             const unsigned d = (unsigned)(key[k] >> shift) & (RADIX - 1);
-            const unsigned peers = __match_any_sync(~0u, d);
+            unsigned peers = ~0u;
+    #pragma unroll
+            for (int b = 0; b < RADIX_BITS; b++) {
+                const bool bit = (d >> b) & 1u;
+                const unsigned bal = __ballot_sync(~0u, bit);
+                peers &= bit ? bal : ~bal;
+            }
             const int leader = __ffs(peers) - 1;
             unsigned prev = 0;
             if (lane == leader)
@@ -516,7 +528,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_onesweep(int pass, K *k0, K
             const K kk = s_keys[i];
             const unsigned dd = (unsigned)(kk >> shift) & (RADIX - 1);
             const unsigned dest = s_glob[dd] + (unsigned)i;
-            if ((int64_t)dest < n) {
+            if (dest < nn) {
                 kdst[dest] = kk;
                 vdst[dest] = s_vals[i];
             }
@@ -622,7 +634,7 @@ void stage_morton_sort(const Work &w, const float *points, cudaStream_t s)
     k_sort_plan<<<1, RADIX, 0, s>>>(w.st, w.n);
     note_launch();
     cudaMemsetAsync(w.sort_lb, 0, (size_t)MAX_PASSES * w.sort_tiles * RADIX * sizeof(unsigned long long), s);
-    const int tiles = (int)std::min<int64_t>(div_up(w.n, SORT_TILE), 2 * (int64_t)w.n_sms);
+    const int tiles = (int)std::min<int64_t>(div_up(w.n, SORT_TILE_MIN), (int64_t)g_sort_blocks_per_sm * w.n_sms);
     for (int pass = 0; pass < MAX_PASSES; pass++)
         k_onesweep<u64><<<tiles, SORT_THREADS, onesweep_smem<u64>(), s>>>(pass, w.keys[0], w.keys[1], w.vals[0],
                                                                           w.vals[1], w.n, w.st, w.sort_lb,
@@ -655,9 +667,20 @@ void stage_gather(const Work &w, const float *points, cudaStream_t s)
 
 void kernels_init_device()
 {
+    int b32 = 0, b64 = 0;
     cudaFuncSetAttribute(k_onesweep<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)onesweep_smem<unsigned long long>());
     cudaFuncSetAttribute(k_onesweep<u32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<u32>());
+    // persistent sort grid: as many blocks as fit on an SM (both key widths
+    // share one grid size)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_onesweep<unsigned long long>, SORT_THREADS,
+                                                      onesweep_smem<unsigned long long>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_onesweep<u32>, SORT_THREADS,
+                                                      onesweep_smem<u32>()) != cudaSuccess) {
+        cudaGetLastError();
+        b32 = b64 = SORT_MIN_BLOCKS;
+    }
+    g_sort_blocks_per_sm = std::max(1, std::min(b32, b64));
 }
 
 }  // namespace abx

@@ -33,6 +33,8 @@ struct Work {
     float4 *nodes;                   // [2 * (2n - 1)] hierarchy records (lo, hi)
     unsigned long long *slot;        // [n] bottom-up meeting slots (global phase)
     int4 *frontier;                  // [n] nodes that finish the build in the global phase
+    int4 *cand;                      // [L] candidate leaves 0-3 of each leaf (aliases frontier, dead after the build)
+    int2 *cand2;                     // [L] candidate leaves 4-5 (aliases slot, dead after the build)
     int *right_of;                   // [n] right child of each internal node
     int *parent;                     // [n] union-find parents (sorted positions)
     unsigned char *core;             // [n] core flags
@@ -83,7 +85,7 @@ void tree_init_device();
 // launching stream at each stage boundary).
 enum Stage {
     ST_BOUNDS = 0, ST_MORTON, ST_SORT, ST_GATHER, ST_CELLS, ST_LEAVES, ST_BUILD,
-    ST_COUNT, ST_UNION, ST_BORDER, ST_FINALIZE, ST_NUM
+    ST_CANDS, ST_COUNT, ST_UNION, ST_BORDER, ST_FINALIZE, ST_NUM
 };
 void prof_begin(cudaStream_t s);
 void prof_mark(int stage, cudaStream_t s);
