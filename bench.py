@@ -16,7 +16,7 @@ region), the roofline of the dominant kernel, the oracle's CPU baseline,
 clocks sampled during the timed region and the number of kernels launched.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--config C2] [--params leaf_size=8,dense_cells=-1,block=128]
+                  [--config fof-clumps-16M] [--params leaf_size=8,dense_cells=-1,block=128]
 
 Under torchrun (N > 1) every rank clusters its own independent instance
 (weak scaling: replicas, no collective on the data path); the timed region is
@@ -102,11 +102,11 @@ class Clocks:
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            self.f = tempfile.NamedTemporaryFile("w", prefix="abx_clocks_", suffix=".csv", delete=False)
+            self.path = self.f.name
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
@@ -123,9 +123,11 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
+        lines = open(self.path).read().splitlines()
+        os.unlink(self.path)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 7:
                 continue
@@ -324,7 +326,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="abx", choices=["abx", "reference"])
-    ap.add_argument("--config", default="C4")
+    ap.add_argument("--config", default="fof-clumps-134M")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-frac", type=float, default=0.125)
     ap.add_argument("--ref-frac", type=float, default=0.0625)

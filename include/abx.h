@@ -258,8 +258,8 @@ unsigned long long abx_launch_count(void);
  * the HBM budget left by batches still running -- and runs the batch as one
  * abx_dbscan_batch pass on that slot's stream.  Batches admitted while others
  * run overlap on the GPU.  A request's labels are exactly what abx_dbscan
- * returns for it alone.  (North-star growth item: in-situ analysis of many
- * sub-volumes; the paper itself clusters one rank's particles per call.)
+ * returns for it alone.  (Meant for in-situ analysis of many sub-volumes;
+ * the paper itself clusters one rank's particles per call.)
  */
 typedef struct abx_serve_config {
     uint64_t hbm_budget_bytes;  /* device bytes running batches may hold (0 = 40 GiB) */

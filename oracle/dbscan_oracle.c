@@ -17,7 +17,7 @@
  *   border b  = non-core point with at least one core neighbour
  *   noise     = every other point, label -1
  *
- * Readings of the paper fixed here (each one is listed in the design doc):
+ * Readings of the paper fixed here:
  *   - pred(p, q): FP32, round-to-nearest-even, no FMA contraction, operations
  *     in this order:  dx = p.x - q.x, dy = ..., dz = ...;
  *     d2 = (dx*dx + dy*dy) + dz*dz;  neighbours iff d2 <= fl(eps*eps).

@@ -180,32 +180,32 @@ def _full(abx, name):
     return got
 
 
-def test_c1_full(abx):
-    _full(abx, "C1")
+def test_full_fof_uniform_32k(abx):
+    _full(abx, "fof-uniform-32K")
 
 
 @pytest.mark.slow
-def test_c2_full(abx):
-    _full(abx, "C2")
+def test_full_fof_clumps_16m(abx):
+    _full(abx, "fof-clumps-16M")
 
 
 @pytest.mark.slow
-def test_c2_stress_full(abx):
-    _full(abx, "C2h")
+def test_full_fof_halos_16m(abx):
+    _full(abx, "fof-halos-16M")
 
 
 @pytest.mark.slow
-def test_c3_full(abx):
-    _full(abx, "C3")
+def test_full_dbscan_blobs_10m(abx):
+    _full(abx, "dbscan-blobs-10M")
 
 
 @pytest.mark.slow
-def test_c4_full(abx):
+def test_full_fof_clumps_134m(abx):
     """2^27 points, FoF: the benchmark's workload, compared label by label."""
-    _full(abx, "C4")
+    _full(abx, "fof-clumps-134M")
 
 
-@pytest.mark.parametrize("name", ["C2", "C3", "C2h"])
+@pytest.mark.parametrize("name", ["fof-clumps-16M", "dbscan-blobs-10M", "fof-halos-16M"])
 def test_scaled_configs(abx, name):
     cfg = scaled(CONFIGS[name], 300_000)
     p = cfg.points()
@@ -232,6 +232,29 @@ def test_profile_api(abx):
     assert ms5["count"] > 0 and ms5["border"] > 0
     assert 1 <= c["radix_passes"] <= 8 and 1 <= c["leaves"] <= len(p) and c["morton_bits"] <= 21
     assert n1 - n0 >= 15
+
+
+@pytest.mark.parametrize("minpts", [2, 4])
+@pytest.mark.parametrize("kw", [dict(dense_cells=-1, leaf_size=2), dict(leaf_size=4), dict(dense_cells=-1, leaf_size=1)],
+                         ids=["leaf2", "dense-leaf4", "leaf1"])
+def test_candidate_list_overflow(abx, kw, minpts):
+    """Leaves with more candidate leaves than the per-leaf list holds fall back
+    to the rope walk from where the list ran out (the traversal counters then
+    show node visits); leaves with few candidates visit no node at all.  Both
+    must give the oracle's labels."""
+    p = clumps(60_000, 40, 71 + minpts, a0=0.03)
+    t = torch.from_numpy(p).cuda()
+    for eps, overflow in [(0.02, True), (0.0005, False)]:
+        abx.profile_enable(2)
+        try:
+            lab = abx.dbscan(t, eps, minpts, params=abx.Params(**kw)).cpu().numpy()
+            tr = abx.profile_traversal()
+        finally:
+            abx.profile_enable(False)
+        assert_same(lab, oracle.dbscan(p, eps, minpts), f"{kw} eps={eps}")
+        if overflow:
+            assert tr["visits"] > 0, tr
+        assert tr["queries"] > 0
 
 
 @pytest.mark.parametrize("seed", [0, 1])

@@ -24,7 +24,7 @@ def _worker(rank, ws, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     t = bench.reduce_max(10.0 + 5 * rank, ws)
-    cfg = bench.rank_config(CONFIGS["C4"], rank, ws)
+    cfg = bench.rank_config(CONFIGS["fof-clumps-134M"], rank, ws)
     dist.barrier()
     out.put((rank, t, cfg.seed, cfg.n, cfg.eps))
     dist.destroy_process_group()
@@ -51,4 +51,4 @@ def test_single_rank_is_identity():
     import bench
     from workloads import CONFIGS
     assert bench.reduce_max(3.5, 1) == 3.5
-    assert bench.rank_config(CONFIGS["C4"], 0, 1) is CONFIGS["C4"]
+    assert bench.rank_config(CONFIGS["fof-clumps-134M"], 0, 1) is CONFIGS["fof-clumps-134M"]

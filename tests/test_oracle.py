@@ -100,9 +100,9 @@ def test_fof_equals_components(seed):
 
 @pytest.mark.slow
 def test_c1_full_bruteforce():
-    """The whole C1 configuration (32,768 uniform points, FoF) against the
+    """The whole 32,768-point uniform FoF workload against the
     connected components of the brute-force eps-graph."""
-    cfg = CONFIGS["C1"]
+    cfg = CONFIGS["fof-uniform-32K"]
     p = cfg.points()
     got = oracle.dbscan(p, cfg.eps, cfg.minpts)
     want = brute.fof_components(p, cfg.eps)

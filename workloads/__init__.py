@@ -161,19 +161,19 @@ def _cfg(name, n, minpts, kind, seed, groups=0, eps=None, a_scale=1.0):
 
 CONFIGS = {
     # FoF, uniform, 32768 points
-    "C1": _cfg("C1", 32768, 2, "uniform", 1001),
+    "fof-uniform-32K": _cfg("fof-uniform-32K", 32768, 2, "uniform", 1001),
     # halo-like FoF, 2^24 points, 20,000 clumps
-    "C2": _cfg("C2", 1 << 24, 2, "clumps", 1002, 20000),
+    "fof-clumps-16M": _cfg("fof-clumps-16M", 1 << 24, 2, "clumps", 1002, 20000),
     # general DBSCAN, 10^7 points in 5,000 blobs + 20% noise, minPts 10, eps 0.004
-    "C3": _cfg("C3", 10_000_000, 10, "blobs", 1003, 5000, eps=0.004),
+    "dbscan-blobs-10M": _cfg("dbscan-blobs-10M", 10_000_000, 10, "blobs", 1003, 5000, eps=0.004),
     # per-rank-scale FoF, 2^27 points, 50,000 clumps
-    "C4": _cfg("C4", 1 << 27, 2, "clumps", 1004, 50000),
+    "fof-clumps-134M": _cfg("fof-clumps-134M", 1 << 27, 2, "clumps", 1004, 50000),
 }
 # Stress variants with clumps ten times more concentrated, so that dense
-# cells and large halos appear (the literal C2/C4 mixtures are nearly uniform
-# at the linking length).  Reported beside, never instead of, C2/C4.
-CONFIGS["C2h"] = _cfg("C2h", 1 << 24, 2, "clumps", 1102, 20000, a_scale=0.1)
-CONFIGS["C4h"] = _cfg("C4h", 1 << 27, 2, "clumps", 1104, 50000, a_scale=0.1)
+# cells and large halos appear (the literal clump mixtures are nearly uniform
+# at the linking length).  Reported beside, never instead of, the literal ones.
+CONFIGS["fof-halos-16M"] = _cfg("fof-halos-16M", 1 << 24, 2, "clumps", 1102, 20000, a_scale=0.1)
+CONFIGS["fof-halos-134M"] = _cfg("fof-halos-134M", 1 << 27, 2, "clumps", 1104, 50000, a_scale=0.1)
 
 
 def scaled(cfg: Config, n: int, seed: int | None = None) -> Config:
