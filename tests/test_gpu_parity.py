@@ -252,9 +252,8 @@ def test_candidate_list_overflow(abx, kw, minpts):
         finally:
             abx.profile_enable(False)
         assert_same(lab, oracle.dbscan(p, eps, minpts), f"{kw} eps={eps}")
-        if overflow:
-            assert tr["visits"] > 0, tr
-        assert tr["queries"] > 0
+        if overflow:  # (at the small eps a minPts > 2 run has no core point, hence no query)
+            assert tr["queries"] > 0 and tr["visits"] > 0, tr
 
 
 @pytest.mark.parametrize("seed", [0, 1])
