@@ -201,8 +201,14 @@ def test_full_dbscan_blobs_10m(abx):
 
 @pytest.mark.slow
 def test_full_fof_clumps_134m(abx):
-    """2^27 points, FoF: the benchmark's workload, compared label by label."""
-    _full(abx, "fof-clumps-134M")
+    """2^27 points, FoF: the benchmark's workload, compared label by label with
+    the library defaults and with the parameters the benchmark runs (the
+    autotuner's pick on this workload: leaf 8, dense cells off, block 128)."""
+    got = _full(abx, "fof-clumps-134M")
+    cfg = CONFIGS["fof-clumps-134M"]
+    bench = gpu_labels(abx, cfg.points(), cfg.eps, cfg.minpts,
+                       abx.Params(leaf_size=8, dense_cells=-1, block=128))
+    assert_same(bench, got, "benchmark parameters")
 
 
 @pytest.mark.parametrize("name", ["fof-clumps-16M", "dbscan-blobs-10M", "fof-halos-16M"])
