@@ -413,9 +413,12 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t n, const State *__rest
         if (r != i)
             lab = min(orig_of(spts, r), bmin[r]);
     }
-    // labels were preset to -1: only cluster members are scattered
+    // labels were preset to -1: only cluster members are scattered (noise
+    // points, most points of a sparse scene, read nothing more)
+    if (lab < 0)
+        return;
     const int o = __float_as_int(spts[i].w);
-    if (lab >= 0 && (unsigned)o < (unsigned)n)
+    if ((unsigned)o < (unsigned)n)
         labels[o] = SEG ? lab - off[s] : lab;
 }
 
