@@ -155,7 +155,6 @@ static void carve(Carver &c, Work &w, int64_t n, int nseg)
     w.slot = c.take<unsigned long long>(N);
     w.frontier = c.take<int4>(N);
     w.cand = w.frontier;
-    w.cand2 = reinterpret_cast<int2 *>(w.slot);
     w.right_of = c.take<int>(N);
     w.parent = c.take<int>(N);
     w.core = c.take<unsigned char>(N);

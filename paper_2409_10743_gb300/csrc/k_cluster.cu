@@ -48,16 +48,17 @@ __device__ __forceinline__ float4 node_hi(const Tree &t, int i) { return __ldg(t
 // own box distance), so one traversal per leaf with the leaf's box finds the
 // leaves after it that any of its points can reach: its candidate leaves.
 // Each point then tests only the points of those leaves and visits no node.
-// Up to CAND_K - 1 candidates are kept; when there are more, the last slot
+// Up to CAND_K - 1 candidates are kept (one int4 per leaf); when there are
+// more, the last slot
 // holds -(node + 2) for the leaf node where the list ran out, and the points
 // walk the ropes from there on with their own box tests (which visits that
 // leaf and everything after it in pre-order).  -1 ends a list.
 
-constexpr int CAND_K = 6;
+constexpr int CAND_K = 4;
 
 template <bool SEG>
 __global__ void k_cand(const State *__restrict__ st, const SegState *__restrict__ seg,
-                       const int *__restrict__ leaf_seg, const float4 *__restrict__ nodes, int4 *cand, int2 *cand2,
+                       const int *__restrict__ leaf_seg, const float4 *__restrict__ nodes, int4 *cand,
                        unsigned *dev_status)
 {
     const int L = st->n_leaves;
@@ -94,7 +95,6 @@ __global__ void k_cand(const State *__restrict__ st, const SegState *__restrict_
         node = __float_as_int(hi.w);
     }
     cand[a] = make_int4(out[0], out[1], out[2], out[3]);
-    cand2[a] = make_int2(out[4], out[5]);
 }
 
 // ---- pair traversal with union-find ------------------------------------------------
@@ -111,8 +111,8 @@ struct TravStats {
 template <bool FOF, bool STATS>
 __device__ __forceinline__ void union_query(const int i, const float e2, const Tree &T,
                                             const float4 *__restrict__ spts, const int *__restrict__ leaf_of,
-                                            const int4 *__restrict__ cand, const int2 *__restrict__ cand2, int *parent,
-                                            unsigned char *core, unsigned *dev_status, TravStats *stats)
+                                            const int4 *__restrict__ cand, int *parent, unsigned char *core,
+                                            unsigned *dev_status, TravStats *stats)
 {
     const int L = T.L;
     const float4 p = spts[i];
@@ -182,17 +182,20 @@ __device__ __forceinline__ void union_query(const int i, const float e2, const T
     };
     const int me = my_leaf - (L - 1);
     const int4 c4 = cand[me];
-    const int2 c2 = cand2[me];
     int resume = SENTINEL;
     for (int c = 0; c < CAND_K; c++) {
-        const int v = c == 0 ? c4.x : c == 1 ? c4.y : c == 2 ? c4.z : c == 3 ? c4.w : c == 4 ? c2.x : c2.y;
+        const int v = c == 0 ? c4.x : c == 1 ? c4.y : c == 2 ? c4.z : c4.w;
         if (v == SENTINEL)
             break;
         if (v < 0) {
             resume = -v - 2;
             break;
         }
-        test_leaf(__float_as_uint(node_lo(T, L - 1 + v).w), leaf_first[v + 1]);
+        // the leaf passed the leaf-box test; the point's own box test is
+        // tighter and spares the point tests of most far leaves
+        const float4 lo = node_lo(T, L - 1 + v), hi = node_hi(T, L - 1 + v);
+        if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2)
+            test_leaf(__float_as_uint(lo.w), leaf_first[v + 1]);
     }
     // more candidates than the list holds: the plain pair traversal from the
     // leaf where the list ran out
@@ -228,7 +231,7 @@ template <bool FOF, bool STATS>
 __global__ void __launch_bounds__(1024, 2) k_union(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
                         const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
                         const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
-                        const int4 *__restrict__ cand, const int2 *__restrict__ cand2, int *parent,
+                        const int4 *__restrict__ cand, int *parent,
                         unsigned char *core, unsigned *dev_status, TravStats *stats)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(1024, 2) k_union(int64_t n, const State *__res
     if (!FOF && !core[i])
         return;
     const Tree T{nodes, leaf_first, st->n_leaves};
-    union_query<FOF, STATS>(i, seg[0].e2, T, spts, leaf_of, cand, cand2, parent, core, dev_status, stats);
+    union_query<FOF, STATS>(i, seg[0].e2, T, spts, leaf_of, cand, parent, core, dev_status, stats);
 }
 
 // Many segments: each query takes its segment's eps and mode from its key.
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(1024, 2) k_union_seg(int64_t n, const State *_
                             const unsigned long long *k0, const unsigned long long *k1,
                             const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
                             const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
-                        const int4 *__restrict__ cand, const int2 *__restrict__ cand2, int *parent,
+                        const int4 *__restrict__ cand, int *parent,
                             unsigned char *core, unsigned *dev_status, TravStats *stats)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -257,9 +260,9 @@ __global__ void __launch_bounds__(1024, 2) k_union_seg(int64_t n, const State *_
     const SegState &g = seg[seg_of_key(sorted_key(st, k0, k1, i), st->shift)];
     const Tree T{nodes, leaf_first, st->n_leaves};
     if (g.minpts <= 2)
-        union_query<true, STATS>(i, g.e2, T, spts, leaf_of, cand, cand2, parent, core, dev_status, stats);
+        union_query<true, STATS>(i, g.e2, T, spts, leaf_of, cand, parent, core, dev_status, stats);
     else if (core[i])
-        union_query<false, STATS>(i, g.e2, T, spts, leaf_of, cand, cand2, parent, core, dev_status, stats);
+        union_query<false, STATS>(i, g.e2, T, spts, leaf_of, cand, parent, core, dev_status, stats);
 }
 
 // ---- core counting with early termination (minPts > 2) -------------------------------
@@ -429,19 +432,19 @@ void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t
     TravStats *stats = (TravStats *)w.stats;
     cudaMemsetAsync(labels, 0xff, (size_t)w.n * sizeof(int32_t), s);  // noise = -1
     if (w.nseg == 1)
-        k_cand<false><<<div_up(w.n, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.cand, w.cand2, w.dev_status);
+        k_cand<false><<<div_up(w.n, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.cand, w.dev_status);
     else
-        k_cand<true><<<div_up(w.n, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.cand, w.cand2, w.dev_status);
+        k_cand<true><<<div_up(w.n, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.cand, w.dev_status);
     note_launch();
     prof_mark(ST_CANDS, s);
     if (w.nseg == 1) {
         if (w.any_fof) {
             if (stats)
                 k_union<true, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                    w.cand, w.cand2, w.parent, w.core, w.dev_status, stats);
+                                                    w.cand, w.parent, w.core, w.dev_status, stats);
             else
                 k_union<true, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                     w.cand, w.cand2, w.parent, w.core, w.dev_status, nullptr);
+                                                     w.cand, w.parent, w.core, w.dev_status, nullptr);
             note_launch();
             prof_mark(ST_UNION, s);
         } else {
@@ -451,10 +454,10 @@ void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t
             prof_mark(ST_COUNT, s);
             if (stats)
                 k_union<false, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                     w.cand, w.cand2, w.parent, w.core, w.dev_status, stats);
+                                                     w.cand, w.parent, w.core, w.dev_status, stats);
             else
                 k_union<false, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                      w.cand, w.cand2, w.parent, w.core, w.dev_status, nullptr);
+                                                      w.cand, w.parent, w.core, w.dev_status, nullptr);
             note_launch();
             prof_mark(ST_UNION, s);
             k_border<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
@@ -473,10 +476,10 @@ void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t
         }
         if (stats)
             k_union_seg<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_of,
-                                              w.leaf_first, w.cand, w.cand2, w.parent, w.core, w.dev_status, stats);
+                                              w.leaf_first, w.cand, w.parent, w.core, w.dev_status, stats);
         else
             k_union_seg<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_of,
-                                               w.leaf_first, w.cand, w.cand2, w.parent, w.core, w.dev_status, nullptr);
+                                               w.leaf_first, w.cand, w.parent, w.core, w.dev_status, nullptr);
         note_launch();
         prof_mark(ST_UNION, s);
         if (w.any_dbscan) {

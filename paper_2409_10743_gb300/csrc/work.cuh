@@ -33,8 +33,7 @@ struct Work {
     float4 *nodes;                   // [2 * (2n - 1)] hierarchy records (lo, hi)
     unsigned long long *slot;        // [n] bottom-up meeting slots (global phase)
     int4 *frontier;                  // [n] nodes that finish the build in the global phase
-    int4 *cand;                      // [L] candidate leaves 0-3 of each leaf (aliases frontier, dead after the build)
-    int2 *cand2;                     // [L] candidate leaves 4-5 (aliases slot, dead after the build)
+    int4 *cand;                      // [L] candidate leaves of each leaf (aliases frontier, dead after the build)
     int *right_of;                   // [n] right child of each internal node
     int *parent;                     // [n] union-find parents (sorted positions)
     unsigned char *core;             // [n] core flags
