@@ -56,7 +56,7 @@ def stage_bytes(stage: str, c: dict, n: int) -> float:
         "cells": 8.0 + 4.0,                               # keys, dense-root preset
         "leaves": 4.0 + 4.0 + 16.0 + per_leaf * (32.0 + 16.0 + 1.0),  # dense root, leaf id, points; leaf records
         "build": per_leaf * (32.0 + 1.0 + 32.0 + 8.0 + 4.0 + 8.0),      # leaf box, delta, node, slot, child, rope
-        "candidates": per_leaf * (32.0 + 24.0),                   # leaf record, candidate list
+        "candidates": per_leaf * (32.0 + 16.0),                   # leaf record, candidate list (int4)
         "count": 16.0 + 1.0,
         "union": 16.0 + 4.0 + 4.0 + 1.0 + per_leaf * 2 * 32.0,        # point, leaf id, parent, core; nodes once
         "border": 16.0 + 1.0,
