@@ -9,6 +9,9 @@
 // O(n) memory), and the merging kernel uses pair traversal (subsection "Pair
 // traversal"): the thread of point i starts at its own leaf and follows ropes,
 // so it only meets leaves after its own and each pair is seen exactly once.
+// Here that traversal runs in two passes: once per leaf with the leaf's box
+// (k_cand: which leaves after it any of its points can reach), then once per
+// point over those candidate leaves only (k_union).
 //
 // The paper's border step (the first core to arrive claims an unclaimed
 // non-core neighbour inside a critical section) is nondeterministic.  It is
