@@ -346,6 +346,19 @@ abx_status abx_bvh_count(const abx_bvh *bvh, const float *queries, int64_t nq, f
                          int32_t cap, int32_t *counts, abx_stream stream);
 
 /*
+ * abx_bvh_first_hit -- early-terminated existence query (paper, subsection
+ * "Early termination", with the traversal stopped at the first neighbour):
+ * hits[q] = the original index (position in the points given to
+ * abx_bvh_build) of a tree point p with pred(query q, p), namely the first
+ * one the traversal meets, or -1 if there is none.  Which neighbour is
+ * returned depends on the hierarchy; that one exists does not.
+ *   queries  device float32 [nq][3];  hits device int32 [nq].
+ * ABX_EINVAL for a null handle or pointers, nq < 0, negative or non-finite eps.
+ */
+abx_status abx_bvh_first_hit(const abx_bvh *bvh, const float *queries, int64_t nq, float eps,
+                             int32_t *hits, abx_stream stream);
+
+/*
  * abx_bvh_pair_histogram -- the "find every pair within a radius, apply F"
  * form of pair traversal (paper, subsection "Pair traversal": forces,
  * 2-point correlation counts), with F = count by distance: hist[b] = number of

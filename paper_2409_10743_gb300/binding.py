@@ -62,6 +62,7 @@ _SIGS = {
     "abx_dbscan_batch": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "abx_bvh_build": (_i32, [_vp, _i64, _i32, ctypes.POINTER(_vp), _vp]),
     "abx_bvh_count": (_i32, [_vp, _vp, _i64, _f32, _i32, _vp, _vp]),
+    "abx_bvh_first_hit": (_i32, [_vp, _vp, _i64, _f32, _vp, _vp]),
     "abx_bvh_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32), _vp]),
     "abx_bvh_destroy": (_i32, [_vp]),
     "abx_profile_enable": (_i32, [_i32]),
@@ -262,7 +263,8 @@ def launch_count() -> int:
 
 
 class BVH:
-    """abx_bvh handle: build over device points, early-terminated counts."""
+    """abx_bvh handle: build over device points, early-terminated counts and
+    first hits, pair-distance histograms."""
 
     def __init__(self, points, leaf_size: int = 0, stream=None):
         p = _points_dev(points)
@@ -280,6 +282,18 @@ class BVH:
         rc = lib().abx_bvh_count(self._h, q.data_ptr(), q.shape[0], float(np.float32(eps)), int(cap),
                                  out.data_ptr(), self._stream)
         _check(rc, "abx_bvh_count")
+        return out
+
+    def first_hit(self, queries, eps: float, out=None):
+        """Original index of one tree point within eps of each query (the
+        first the traversal meets), -1 where there is none."""
+        import torch
+        q = _points_dev(queries)
+        if out is None:
+            out = torch.empty(q.shape[0], dtype=torch.int32, device=q.device)
+        rc = lib().abx_bvh_first_hit(self._h, q.data_ptr(), q.shape[0], float(np.float32(eps)), out.data_ptr(),
+                                     self._stream)
+        _check(rc, "abx_bvh_first_hit")
         return out
 
     def pair_histogram(self, r_edges):

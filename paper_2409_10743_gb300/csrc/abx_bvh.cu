@@ -1,7 +1,8 @@
 // The hierarchy as a handle of its own: build once, then run early-terminated
-// range counts against it (paper, subsections "Callbacks" and "Early
-// termination": a callback's return value may stop a query's traversal, e.g.
-// once a count is reached).
+// range queries against it -- counts capped at a value, and the first hit
+// (paper, subsections "Callbacks" and "Early termination": a callback's return
+// value may stop a query's traversal, e.g. once a count is reached or a
+// neighbour is found).
 #include <cstring>
 
 #include "work.cuh"
@@ -49,6 +50,47 @@ __global__ void k_count_ext(const float *__restrict__ q, int64_t nq, const State
         node = __float_as_int(hi.w);
     }
     counts[k] = cnt;
+}
+
+// First hit: the traversal of k_count_ext stopped at the first point within
+// eps; hits[k] = that point's original index, -1 if there is none.  Which
+// neighbour is found depends on the hierarchy (the first in its pre-order),
+// so only "a neighbour, or none" is the contract.
+__global__ void k_first_hit(const float *__restrict__ q, int64_t nq, const State *__restrict__ st,
+                            const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                            const int *__restrict__ leaf_first, float e2, int32_t *hits, unsigned *dev_status)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nq)
+        return;
+    const float px = __ldg(q + 3 * k), py = __ldg(q + 3 * k + 1), pz = __ldg(q + 3 * k + 2);
+    const int L = st->n_leaves;
+    int hit = -1, node = st->root;
+    unsigned steps = 0;
+    while (node != SENTINEL && hit < 0) {
+        if ((unsigned)node >= (unsigned)(2 * L - 1) || ++steps > (unsigned)(2 * L)) {
+            atomicOr(dev_status, DEV_INTERNAL);
+            break;
+        }
+        const float4 lo = __ldg(nodes + 2 * (size_t)node), hi = __ldg(nodes + 2 * (size_t)node + 1);
+        if (box_dist2_rn(px, py, pz, lo, hi) <= e2) {
+            if (node < L - 1) {
+                node = __float_as_int(lo.w);
+                continue;
+            }
+            const int s = (int)(__float_as_uint(lo.w) & ~DENSE_BIT);
+            const int e = leaf_first[node - (L - 1) + 1];
+            for (int j = s; j < e; j++) {
+                const float4 p = __ldg(spts + j);
+                if (dist2_rn(px, py, pz, p.x, p.y, p.z) <= e2) {
+                    hit = __float_as_int(p.w);
+                    break;
+                }
+            }
+        }
+        node = __float_as_int(hi.w);
+    }
+    hits[k] = hit;
 }
 
 // Depth of each leaf: descend from the root; internal node p splits leaves
@@ -125,6 +167,24 @@ abx_status abx_bvh_count(const abx_bvh *bvh, const float *queries, int64_t nq, f
     const float e2 = eps * eps;
     k_count_ext<<<div_up(nq, 256), 256, 0, s>>>(queries, nq, bvh->w.st, bvh->w.spts, bvh->w.nodes,
                                                 bvh->w.leaf_first, e2, cap, counts, bvh->w.dev_status);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? ABX_OK : ABX_ECUDA;
+}
+
+abx_status abx_bvh_first_hit(const abx_bvh *bvh, const float *queries, int64_t nq, float eps, int32_t *hits,
+                             abx_stream stream)
+{
+    if (!bvh || nq < 0 || nq > INT32_MAX || !(eps >= 0.0f) || eps == __builtin_inff())
+        return ABX_EINVAL;
+    if (nq == 0)
+        return ABX_OK;
+    if (!queries || !hits)
+        return ABX_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float e2 = eps * eps;
+    k_first_hit<<<div_up(nq, 256), 256, 0, s>>>(queries, nq, bvh->w.st, bvh->w.spts, bvh->w.nodes,
+                                                bvh->w.leaf_first, e2, hits, bvh->w.dev_status);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? ABX_OK : ABX_ECUDA;
 }
 

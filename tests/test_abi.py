@@ -98,6 +98,7 @@ def test_bvh_arguments_rejected_on_host(lib):
     assert lib.abx_bvh_build(fake, 10, 64, ctypes.byref(h), null) == ABX_EINVAL
     assert lib.abx_bvh_build(null, 10, 0, ctypes.byref(h), null) == ABX_EINVAL
     assert lib.abx_bvh_count(null, fake, 1, 0.1, 1, fake, null) == ABX_EINVAL
+    assert lib.abx_bvh_first_hit(null, fake, 1, 0.1, fake, null) == ABX_EINVAL
     assert lib.abx_bvh_destroy(null) == ABX_EINVAL
 
 

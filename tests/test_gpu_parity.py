@@ -169,6 +169,32 @@ def test_bvh_count_early_termination(abx):
     h.close()
 
 
+@pytest.mark.parametrize("leaf_size", [1, 4, 8])
+def test_bvh_first_hit(abx, leaf_size):
+    """A first hit is some tree point within eps of the query (several can be
+    right: check that the one returned is), and -1 exactly where no tree point
+    is within eps (brute force)."""
+    import brute
+    rng = np.random.default_rng(19 + leaf_size)
+    p = _clumpy(rng, 20000, 10, 0.02)
+    q = np.concatenate([_clumpy(rng, 2000, 10, 0.02), rng.random((500, 3), dtype=np.float32) * 1.2 - 0.1])
+    q = q.astype(np.float32)
+    h = abx.BVH(torch.from_numpy(p).cuda(), leaf_size=leaf_size)
+    for eps in (0.0, 0.004, 0.02):
+        got = h.first_hit(torch.from_numpy(q).cuda(), eps).cpu().numpy()
+        torch.cuda.synchronize()
+        assert abx.device_status() == 0
+        has = np.array([brute.adjacency_rows(np.concatenate([q[i:i + 1], p]), eps, slice(0, 1))[0, 1:].any()
+                        for i in range(len(q))])
+        assert np.array_equal(got >= 0, has), f"eps={eps}"
+        for i in np.nonzero(got >= 0)[0]:
+            assert 0 <= got[i] < len(p) and oracle.pred(q[i], p[got[i]], eps), (i, got[i])
+    # points of the tree itself always hit (eps = 0: an exact duplicate, themselves)
+    got = h.first_hit(torch.from_numpy(p[:300]).cuda(), 0.0).cpu().numpy()
+    assert np.all(got >= 0) and np.all(np.all(p[got] == p[:300], axis=1))
+    h.close()
+
+
 # ---- full-size configurations ------------------------------------------------------
 
 def _full(abx, name):
