@@ -81,16 +81,18 @@ def hbm_peak() -> tuple[float, str]:
 
 
 def ncu_traffic(stage: str):
-    """DRAM bytes per launch of the stage's kernel from the committed ncu
-    summary, when it was taken on the current kernel sources (else None)."""
+    """DRAM bytes per point per launch of the stage's kernel from the committed
+    ncu summary, when it was taken on the current source of that kernel (its
+    file and the device headers; else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         from paper_2409_10743_gb300 import build as b
-        if d.get("csrc_sha") != b.source_hash():
+        e = d.get("stages", {}).get(stage, {})
+        if not e.get("source") or e.get("source_sha") != b.kernel_source_hash(e["source"]):
             return None
-        return d.get("stages", {}).get(stage, {}).get("dram_bytes_per_point_launch")
+        return e.get("dram_bytes_per_point_launch")
     except Exception:
         return None
 

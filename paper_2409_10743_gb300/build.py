@@ -49,6 +49,17 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def kernel_source_hash(cu_file: str) -> str:
+    """sha256 over one kernel file and the device headers every kernel file
+    includes (identifies the kernels of that file a profile was taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in [cu_file, "abx_internal.cuh", "work.cuh", "scan.cuh"]:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
