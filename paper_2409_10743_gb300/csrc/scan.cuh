@@ -71,6 +71,29 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_flag_scan(int64_t n, F f, int 
     }
     __syncthreads();
     unsigned long long run = s_excl + wpre + x - c;  // flags before this thread's first item
+    if (base + SCAN_ITEMS <= n && (reinterpret_cast<uintptr_t>(ids + base) & 15) == 0) {
+        // a whole run of items: the ids leave as SCAN_ITEMS / 4 vector stores
+        // (a thread's items are consecutive, so scalar stores would touch a
+        // different sector per lane for every item)
+        int v[SCAN_ITEMS];
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j++) {
+            if (flags & (1u << j)) {
+                first[run] = (int)(base + j);
+                run++;
+            }
+            v[j] = (int)run - 1;
+        }
+        int4 *dst = reinterpret_cast<int4 *>(ids + base);
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS / 4; q++)
+            dst[q] = make_int4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        if (base + SCAN_ITEMS == n) {
+            first[run] = (int)n;
+            *total_out = (int)run;
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < SCAN_ITEMS; j++) {
         int64_t pos = base + j;
