@@ -50,11 +50,21 @@ def source_hash() -> str:
 
 
 def kernel_source_hash(cu_file: str) -> str:
-    """sha256 over one kernel file and the device headers every kernel file
-    includes (identifies the kernels of that file a profile was taken on)."""
+    """sha256 over one kernel file and the csrc headers it includes, followed
+    transitively (identifies the kernels of that file a profile was taken on;
+    the public header only declares the host API)."""
     import hashlib
+    import re
+    seen, todo = [], [cu_file]
+    while todo:
+        name = todo.pop(0)
+        if name in seen:
+            continue
+        seen.append(name)
+        with open(os.path.join(CSRC, name)) as f:
+            todo += [m for m in re.findall(r'#include\s+"([^"/]+)"', f.read())]
     h = hashlib.sha256()
-    for name in [cu_file, "abx_internal.cuh", "work.cuh", "scan.cuh"]:
+    for name in seen:
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
