@@ -50,12 +50,12 @@ __device__ __forceinline__ float4 node_hi(const Tree &t, int i) { return __ldg(t
 // every point of the leaf (box_box_dist2_rn is a lower bound of the point's
 // own box distance), so one traversal per leaf with the leaf's box finds the
 // leaves after it that any of its points can reach: its candidate leaves.
-// Each point then tests only the points of those leaves and visits no node.
-// Up to CAND_K - 1 candidates are kept (one int4 per leaf); when there are
-// more, the last slot
-// holds -(node + 2) for the leaf node where the list ran out, and the points
-// walk the ropes from there on with their own box tests (which visits that
-// leaf and everything after it in pre-order).  -1 ends a list.
+// Each point then tests only the points of those leaves (after its own box
+// test of each) and visits no node.  Up to CAND_K - 1 candidates are kept (one
+// int4 per leaf); when there are more, the last slot holds -(node + 2) for
+// the leaf node where the list ran out, and the points walk the ropes from
+// there on with their own box tests (which visits that leaf and everything
+// after it in pre-order).  -1 ends a list.
 
 constexpr int CAND_K = 4;
 
