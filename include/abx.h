@@ -123,6 +123,31 @@ abx_status abx_dbscan_host(const float *points_host, int64_t n, float eps, int32
                            int32_t *labels_host, abx_stream stream);
 
 /*
+ * CUDA graph of one fixed clustering.  abx_graph_create captures every stage
+ * of abx_dbscan_ex for these arguments (the same pointers, n, eps, minPts and
+ * parameters) into a CUDA graph with a device workspace of its own, so that
+ * abx_graph_launch replays the ~29 kernels with one launch: for small inputs
+ * the launches, not the kernels, set the time.  The caller may change the
+ * CONTENTS of points between replays (a simulation's next time step), not
+ * the buffers or n; each replay writes labels for the current contents.
+ *   points, n (1 <= n <= 2^31 - 1), eps, minpts, labels, params: as for
+ *           abx_dbscan_ex (params NULL = the autotuner's pick or defaults)
+ *   out     receives the handle
+ * Allocates the workspace (cudaMalloc) and synchronises during creation;
+ * ABX_ENOMEM if the workspace does not fit, ABX_ECUDA if capture fails.
+ * abx_graph_launch enqueues one replay on `stream` (ABX_EINVAL if the current
+ * device is not the one the graph was made on); replays on different streams
+ * share the workspace, so keep them in order on one stream.
+ * abx_graph_destroy waits for the device, then frees the graph and its
+ * workspace.
+ */
+typedef struct abx_graph abx_graph;
+abx_status abx_graph_create(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
+                            const abx_params *params, abx_graph **out);
+abx_status abx_graph_launch(abx_graph *graph, abx_stream stream);
+abx_status abx_graph_destroy(abx_graph *graph);
+
+/*
  * abx_device_status -- wait for `stream`, then return and clear the current
  * device's status word: ABX_OK, ABX_ENONFINITE (a coordinate was not finite),
  * ABX_ETIMEOUT (a bounded device wait ran out) or ABX_EINTERNAL (a kernel's
@@ -187,7 +212,7 @@ abx_status abx_dbscan_noalloc(const float *points, int64_t n, float eps, int32_t
 abx_status abx_cluster_stats(const float *points, const int32_t *labels, int64_t n, int32_t *n_clusters,
                              int32_t *ids, int32_t *sizes, float *centres, float *radii, abx_stream stream);
 
-/* ---- autotuning (spec growth item; the paper lists runtime tuning of
+/* ---- autotuning (the paper lists runtime tuning of
  *      occupancy parameters as future work, section "Conclusions") --------- */
 
 /*

@@ -58,6 +58,9 @@ _SIGS = {
     "abx_dbscan": (_i32, [_vp, _i64, _f32, _i32, _vp, _vp]),
     "abx_dbscan_ex": (_i32, [_vp, _i64, _f32, _i32, _vp, ctypes.POINTER(Params), _vp]),
     "abx_dbscan_host": (_i32, [_vp, _i64, _f32, _i32, _vp, _vp]),
+    "abx_graph_create": (_i32, [_vp, _i64, _f32, _i32, _vp, _vp, _vp]),
+    "abx_graph_launch": (_i32, [_vp, _vp]),
+    "abx_graph_destroy": (_i32, [_vp]),
     "abx_device_status": (_i32, [_vp]),
     "abx_dbscan_batch": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "abx_bvh_build": (_i32, [_vp, _i64, _i32, ctypes.POINTER(_vp), _vp]),
@@ -145,6 +148,41 @@ def dbscan(points, eps: float, minpts: int, labels=None, params: Params | None =
                                      ctypes.byref(params), s)
     _check(rc, "abx_dbscan")
     return labels
+
+
+class Graph:
+    """abx_graph: the whole clustering of one fixed input (these device
+    buffers, eps, minPts, parameters) captured as a CUDA graph; launch()
+    replays it on the current contents of the points."""
+
+    def __init__(self, points, eps: float, minpts: int, labels=None, params: Params | None = None):
+        import torch
+        self.points = _points_dev(points)
+        n = self.points.shape[0]
+        self.labels = labels if labels is not None else torch.empty(n, dtype=torch.int32, device=self.points.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.points.device):
+            rc = lib().abx_graph_create(self.points.data_ptr(), n, float(np.float32(eps)), int(minpts),
+                                        self.labels.data_ptr(), ctypes.byref(params) if params is not None else None,
+                                        ctypes.byref(self._h))
+        _check(rc, "abx_graph_create")
+
+    def launch(self, stream=None):
+        import torch
+        with torch.cuda.device(self.points.device):
+            _check(lib().abx_graph_launch(self._h, _stream(stream)), "abx_graph_launch")
+        return self.labels
+
+    def close(self):
+        if self._h:
+            _check(lib().abx_graph_destroy(self._h), "abx_graph_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dbscan_host(points: np.ndarray, eps: float, minpts: int, labels: np.ndarray | None = None, stream=None):

@@ -80,11 +80,20 @@ static State *g_prof_state = nullptr;  // pinned host copy of the last profiled 
 static unsigned long long *g_stats_dev = nullptr;   // traversal counters (mode 2)
 static unsigned long long g_stats_host[8];
 
-void note_launch(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+// Kernels launched by this host thread (a graph capture counts its own).
+static thread_local unsigned long long t_launches = 0;
+// Set while this thread captures a graph: no profile events go into it.
+static thread_local bool t_capturing = false;
+
+void note_launch(int k)
+{
+    g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed);
+    t_launches += (unsigned long long)k;
+}
 
 void prof_begin(cudaStream_t s)
 {
-    if (!g_prof_on.load())
+    if (!g_prof_on.load() || t_capturing)
         return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_ev_ready) {
@@ -101,7 +110,7 @@ void prof_begin(cudaStream_t s)
 
 void prof_mark(int stage, cudaStream_t s)
 {
-    if (!g_prof_on.load())
+    if (!g_prof_on.load() || t_capturing)
         return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_ev_ready || stage < 0 || stage >= ST_NUM)
@@ -232,7 +241,7 @@ static void run_stages(Work &w, const float *points, int32_t *labels, const Para
     stage_cells_leaves(w, p, s);
     stage_hierarchy(w, s);
     stage_cluster(w, p, labels, s);
-    if (g_prof_on.load()) {
+    if (g_prof_on.load() && !t_capturing) {
         std::lock_guard<std::mutex> lk(g_prof_mu);
         if (!g_prof_state && cudaMallocHost((void **)&g_prof_state, sizeof(State)) != cudaSuccess) {
             g_prof_state = nullptr;
@@ -329,6 +338,111 @@ abx_status abx_dbscan(const float *points, int64_t n, float eps, int32_t minpts,
                       abx_stream stream)
 {
     return abx_dbscan_ex(points, n, eps, minpts, labels, nullptr, stream);
+}
+
+// ---- the whole clustering of one fixed input as a CUDA graph ----------------------
+
+struct abx_graph {
+    int device = -1;
+    void *ws = nullptr;           // the graph's own workspace (cudaMalloc)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;  // kernels per replay
+};
+
+static void graph_free(abx_graph *g)
+{
+    if (g->exec)
+        cudaGraphExecDestroy(g->exec);
+    if (g->graph)
+        cudaGraphDestroy(g->graph);
+    if (g->ws)
+        cudaFree(g->ws);
+    delete g;
+}
+
+abx_status abx_graph_create(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
+                            const abx_params *params, abx_graph **out)
+{
+    if (!out)
+        return ABX_EINVAL;
+    *out = nullptr;
+    abx_status rc = check_args(points, n, eps, minpts, labels);
+    if (rc != ABX_OK || n == 0)
+        return n == 0 ? ABX_EINVAL : rc;
+    Params p;
+    abx_params tuned;
+    if (!params && tune_lookup(n, minpts, &tuned))
+        params = &tuned;
+    if ((rc = resolve_params(params, p)) != ABX_OK)
+        return rc;
+    DeviceCtx *ctx;
+    if ((rc = device_ctx(&ctx)) != ABX_OK)
+        return rc;
+    abx_graph *g = new abx_graph;
+    cudaGetDevice(&g->device);
+    if (cudaMalloc(&g->ws, work_bytes(n)) != cudaSuccess) {
+        cudaGetLastError();
+        g->ws = nullptr;
+        graph_free(g);
+        return ABX_ENOMEM;
+    }
+    Work w;
+    work_carve(w, g->ws, n, 1);
+    w.n_sms = ctx->n_sms;
+    w.dev_status = ctx->status;
+    w.any_fof = minpts <= 2;
+    w.any_dbscan = !w.any_fof;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        graph_free(g);
+        return ABX_ECUDA;
+    }
+    const unsigned long long l0 = t_launches;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        t_capturing = true;
+        stage_segments_single(w, eps, minpts, cs);
+        run_stages(w, points, labels, p, cs);
+        t_capturing = false;
+        e = cudaStreamEndCapture(cs, &g->graph);
+    }
+    g->launches = t_launches - l0;
+    if (e == cudaSuccess)
+        e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        graph_free(g);
+        return ABX_ECUDA;
+    }
+    *out = g;
+    return ABX_OK;
+}
+
+abx_status abx_graph_launch(abx_graph *g, abx_stream stream)
+{
+    if (!g || !g->exec)
+        return ABX_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device)
+        return ABX_EINVAL;
+    if (cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return ABX_ECUDA;
+    }
+    note_launch((int)g->launches);
+    return ABX_OK;
+}
+
+abx_status abx_graph_destroy(abx_graph *g)
+{
+    if (!g)
+        return ABX_EINVAL;
+    cudaDeviceSynchronize();  // no replay may still read the workspace
+    graph_free(g);
+    return ABX_OK;
 }
 
 abx_status abx_dbscan_host(const float *points_host, int64_t n, float eps, int32_t minpts, int32_t *labels_host,

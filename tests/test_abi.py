@@ -71,6 +71,19 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.abx_dbscan_ex(fake, 10, 0.1, 2, fake, ctypes.byref(bad), null) == ABX_EINVAL
 
 
+def test_graph_arguments_rejected_on_host(lib):
+    from paper_2409_10743_gb300.binding import ABX_EINVAL
+    null = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(0x1000)
+    h = ctypes.c_void_p()
+    assert lib.abx_graph_create(fake, 10, 0.1, 2, fake, null, null) == ABX_EINVAL   # no handle
+    assert lib.abx_graph_create(fake, 0, 0.1, 2, fake, null, ctypes.byref(h)) == ABX_EINVAL  # n = 0
+    assert lib.abx_graph_create(fake, 10, -1.0, 2, fake, null, ctypes.byref(h)) == ABX_EINVAL
+    assert lib.abx_graph_create(null, 10, 0.1, 2, fake, null, ctypes.byref(h)) == ABX_EINVAL
+    assert lib.abx_graph_launch(null, null) == ABX_EINVAL
+    assert lib.abx_graph_destroy(null) == ABX_EINVAL
+
+
 def test_batch_arguments_rejected_on_host(lib):
     from paper_2409_10743_gb300.binding import ABX_EINVAL, ABX_OK
     null = ctypes.c_void_p(0)
