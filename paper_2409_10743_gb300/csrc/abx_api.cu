@@ -440,8 +440,15 @@ abx_status abx_graph_destroy(abx_graph *g)
 {
     if (!g)
         return ABX_EINVAL;
+    int cur = -1;
+    const int dev = g->device;
+    cudaGetDevice(&cur);
+    if (cur != dev)
+        cudaSetDevice(dev);
     cudaDeviceSynchronize();  // no replay may still read the workspace
     graph_free(g);
+    if (cur >= 0 && cur != dev)
+        cudaSetDevice(cur);
     return ABX_OK;
 }
 
