@@ -55,6 +55,9 @@ def _load():
                                               ctypes.c_int32, ctypes.c_void_p]
             lib.oracle_pair_count.restype = ctypes.c_int64
             lib.oracle_pair_count.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_float]
+            lib.oracle_pair_list.restype = ctypes.c_int64
+            lib.oracle_pair_list.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p,
+                                             ctypes.c_int64]
             lib.oracle_cluster_stats.restype = ctypes.c_int64
             lib.oracle_cluster_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64] + \
                 [ctypes.c_void_p] * 4
@@ -112,6 +115,19 @@ def pair_count(points, eps: float) -> int:
     if r < 0:
         raise OracleError(_ERRORS.get(int(r), f"error {r}"))
     return int(r)
+
+
+def pairs(points, eps: float) -> np.ndarray:
+    """Every unordered neighbour pair as rows (i, j), i < j, original indices,
+    sorted (int64, shape (m, 2))."""
+    p = _points(points)
+    total = pair_count(p, eps)
+    out = np.zeros((max(total, 1), 2), dtype=np.int64)
+    r = _load().oracle_pair_list(p.ctypes.data, p.shape[0], float(np.float32(eps)), out.ctypes.data, total)
+    if r < 0:
+        raise OracleError(_ERRORS.get(int(r), f"error {r}"))
+    out = out[:total]
+    return out[np.lexsort((out[:, 1], out[:, 0]))]
 
 
 def pred(p, q, eps: float) -> bool:

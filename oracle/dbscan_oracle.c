@@ -472,6 +472,51 @@ int64_t oracle_pair_count(const float *points, int64_t n, float eps)
     return c.pairs;
 }
 
+/*
+ * oracle_pair_list: every unordered pair {i, j}, i < j (original indices),
+ * with pred(i, j) -- the pairs the paper's pair traversal hands to its
+ * callback F exactly once each (section "Pair traversal").  Writes the first
+ * min(total, cap) pairs found to out[2k], out[2k+1] and returns the total.
+ */
+int64_t oracle_pair_list(const float *points, int64_t n, float eps, int64_t *out, int64_t cap);
+
+typedef struct {
+    int64_t pairs, cap;
+    int64_t *out;
+} orc_pair_list;
+
+static int visit_pair_list(void *ctx, int64_t i, int64_t j)
+{
+    orc_pair_list *c = (orc_pair_list *)ctx;
+    if (j > i) {
+        if (c->pairs < c->cap) {
+            c->out[2 * c->pairs] = i;
+            c->out[2 * c->pairs + 1] = j;
+        }
+        c->pairs++;
+    }
+    return 0;
+}
+
+int64_t oracle_pair_list(const float *points, int64_t n, float eps, int64_t *out, int64_t cap)
+{
+    if (n < 0 || n > INT32_MAX || !(eps >= 0.0f) || isinf(eps) || cap < 0 || (cap > 0 && !out))
+        return ORC_EINVAL;
+    if (n == 0)
+        return 0;
+    for (int64_t i = 0; i < 3 * n; i++)
+        if (!isfinite(points[i]))
+            return ORC_ENONFINITE;
+    orc_grid g;
+    int rc = orc_build_grid(&g, points, n, eps);
+    if (rc != ORC_OK)
+        return rc;
+    orc_pair_list c = {0, cap, out};
+    orc_sweep(&g, want_all, visit_pair_list, &c);
+    free(g.s);
+    return c.pairs;
+}
+
 /* ---- consumers of a clustering (plain definitions) ------------------------- */
 
 /*
