@@ -52,7 +52,8 @@ def stage_bytes(stage: str, c: dict, n: int) -> float:
         "bounds": 12.0,                                   # read xyz
         "morton": 12.0 + kb,                              # read xyz, write key
         "sort": (kb + kb + 4.0) + (P - 1) * 2 * (kb + 4.0),  # 1st pass: key in, key+idx out; then both ways
-        "gather": 4.0 + 12.0 + 16.0 + 4.0 + 1.0,          # perm, xyz, sorted float4, parent, core
+        "gather": 4.0 + 12.0 + 16.0,                      # perm, xyz, sorted float4 (the union-find
+                                                          # resets are charged to the traversal's parent RMW)
         "cells": 8.0 + 4.0,                               # keys, dense-root preset
         "leaves": 4.0 + 4.0 + 16.0 + per_leaf * (32.0 + 16.0 + 1.0),  # dense root, leaf id, points; leaf records
         "build": per_leaf * (32.0 + 1.0 + 32.0 + 8.0 + 4.0 + 8.0),      # leaf box, delta, node, slot, child, rope
@@ -63,6 +64,9 @@ def stage_bytes(stage: str, c: dict, n: int) -> float:
         "finalize": 16.0 + 1.0 + 4.0 + 4.0,               # point, core, parent, label
     }
     return table.get(stage, 0.0)
+
+
+TRAVERSAL_BYTES_PER_POINT = 72.0
 
 
 def measured_peaks() -> dict:
@@ -176,7 +180,67 @@ def served_cpu_baseline(reqs, pts) -> dict:
             "sample": f"the same {len(reqs)} requests, one request per thread ({dt:.1f} s)"}
 
 
-def served_benchmark(abx, n_requests: int, rate_hz: float, device: bool, cpu_baseline: bool = False) -> dict:
+def _fill_request(task):
+    """Worker (spawned process): draw request k's points into the shared block."""
+    name, start, k = task
+    from multiprocessing import shared_memory
+
+    from workloads import request_stream
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        r = request_stream(2000)[k]  # sizes do not depend on the arrival rate
+        dst = np.ndarray((r.n, 3), np.float32, buffer=shm.buf, offset=start * 12)
+        dst[:] = r.points()
+    finally:
+        shm.close()
+    return k
+
+
+class RequestPoints:
+    """The points of the first n requests of the seeded stream, drawn in
+    parallel (spawned workers: safe after CUDA is up) into one shared block;
+    pts[k] is request k's (n_k, 3) float32 view."""
+
+    def __init__(self, n_requests: int, rate_hz: float):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+
+        from workloads import request_stream
+        self.reqs = request_stream(2000, rate_hz=rate_hz)[:n_requests]
+        sizes = np.array([r.n for r in self.reqs], np.int64)
+        self.off = np.concatenate([[0], np.cumsum(sizes)])
+        self.shm = shared_memory.SharedMemory(create=True, size=int(self.off[-1]) * 12)
+        order = np.argsort(-sizes, kind="stable")  # largest first: shortest makespan
+        with mp.get_context("spawn").Pool(min(32, os.cpu_count() or 1)) as pool:
+            pool.map(_fill_request, [(self.shm.name, int(self.off[k]), int(k)) for k in order], chunksize=1)
+        self.all = np.ndarray((int(self.off[-1]), 3), np.float32, buffer=self.shm.buf)
+        self.pts = [self.all[self.off[k]:self.off[k + 1]] for k in range(len(self.reqs))]
+
+    def close(self):
+        del self.pts, self.all
+        self.shm.close()
+        self.shm.unlink()
+
+
+def tune_batches(abx, rp: "RequestPoints", dall) -> list:
+    """The batch autotuner on batches of consecutive requests of a few total
+    sizes (the classes the server's batches fall in); each pick is remembered
+    for its class and used by the server."""
+    picks = []
+    for target in (1 << 21, 1 << 23, 1 << 25):
+        k = int(np.searchsorted(rp.off, target))
+        k = max(2, min(k, len(rp.reqs)))
+        if rp.off[k] > (1 << 25):
+            k -= 1
+        reqs = rp.reqs[:k]
+        p = abx.autotune_batch(dall[:int(rp.off[k])], rp.off[:k + 1], [r.eps for r in reqs],
+                               [r.minpts for r in reqs])
+        picks.append({"requests": k, "points": int(rp.off[k]), "params": p})
+    return picks
+
+
+def served_benchmark(abx, n_requests: int, rate_hz: float, device: bool, cpu_baseline: bool = False,
+                     rp: "RequestPoints | None" = None, dall=None, tuned=None) -> dict:
     """The served stream (first n_requests of the 2,000-request stream: Poisson
     arrivals, log-uniform sizes 10^3..10^7, halo mixture, minPts in {2,5,10})
     replayed in real time through (a) the plain path -- one blocking
@@ -190,13 +254,11 @@ def served_benchmark(abx, n_requests: int, rate_hz: float, device: bool, cpu_bas
     import threading
 
     import torch
-    from workloads import request_stream
-    reqs = request_stream(2000, rate_hz=rate_hz)[:n_requests]
-    pts = [r.points() for r in reqs]
+    reqs, pts = rp.reqs[:n_requests], rp.pts[:n_requests]
     lib = abx.lib()
     s_ptr = abx._stream(None)
     if device:
-        dpts = [torch.from_numpy(p).cuda() for p in pts]
+        dpts = [dall[rp.off[k]:rp.off[k + 1]] for k in range(len(reqs))]
         plain_labels = [torch.empty(len(p), dtype=torch.int32, device="cuda") for p in pts]
         torch.cuda.synchronize()
     else:
@@ -271,7 +333,7 @@ def served_benchmark(abx, n_requests: int, rate_hz: float, device: bool, cpu_bas
         all(same(a, b) for a, b in zip(plain_labels, out_s))
     out = {"requests": len(reqs), "rate_hz": rate_hz, "points": int(sum(len(p) for p in pts)),
             "resident": "device (HBM)" if device else "host (pageable numpy)",
-            "sizes": "log-uniform 1e3..1e7, first requests of the seeded 2,000-request stream",
+            "sizes": f"log-uniform 1e3..1e7, the first {len(reqs)} requests of the seeded 2,000-request stream",
             "plain": {**plain_open, "req_per_s": round(plain_rps, 2)},
             "batched": {"p50_ms": round(1e3 * float(np.percentile(lat_o, 50)), 3),
                         "p99_ms": round(1e3 * float(np.percentile(lat_o, 99)), 3),
@@ -280,8 +342,55 @@ def served_benchmark(abx, n_requests: int, rate_hz: float, device: bool, cpu_bas
                         "mean_batch_requests_saturated": round(st_s["mean_batch_requests"], 2),
                         "peak_hbm_bytes": int(st_s["peak_bytes"])},
             "labels_identical": bool(exact)}
-    if cpu_baseline:
-        out["cpu_baseline"] = served_cpu_baseline(reqs, pts)
+    if tuned is not None:
+        out["batch_params"] = tuned
+    if cpu_baseline:  # a bounded sample: the first 120 requests
+        out["cpu_baseline"] = served_cpu_baseline(reqs[:120], pts[:120])
+    return out
+
+
+def other_configs(abx, names, steps: int = 10) -> dict:
+    """The other workloads, one short run each: the autotuner's pick, then
+    `steps` timed clusterings (CUDA events on the launching stream, stage
+    events inside): Mpoints/s, the pair traversal's fraction of the HBM peak
+    on the 72 B/point model, and the whole step's on the stage model."""
+    import torch
+    from workloads import CONFIGS
+    peak, _ = hbm_peak()
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name in names:
+        cfg = CONFIGS[name]
+        p = cfg.points()
+        t = torch.from_numpy(p).cuda()
+        labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+        params = abx.autotune(t, cfg.eps, cfg.minpts)
+        for _ in range(3):
+            abx.dbscan(t, cfg.eps, cfg.minpts, labels=labels)
+        abx.profile_enable(True)
+        torch.cuda.synchronize()
+        stages = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            abx.dbscan(t, cfg.eps, cfg.minpts, labels=labels)
+            stages.append(abx.profile_read())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        counters = abx.profile_counters()
+        abx.profile_enable(False)
+        if abx.device_status() != 0:
+            raise SystemExit(f"device status after {name}")
+        ms = e0.elapsed_time(e1) / steps
+        mean = {k: float(np.mean([s[k] for s in stages])) for k in stages[0]}
+        trav_ms = mean["candidates"] + mean["union"] + mean["count"] + mean["border"]
+        trav = TRAVERSAL_BYTES_PER_POINT * cfg.n / (trav_ms / 1e3) / 1e9 if trav_ms > 0 else 0.0
+        alg = sum(stage_bytes(k, counters, cfg.n) for k in mean) * cfg.n
+        out[name] = {"workload": cfg.describe(), "mpts_s": round(cfg.n / ms / 1e3, 1), "ms_per_step": round(ms, 3),
+                     "traversal_frac": round(trav / peak, 4), "pipeline_frac": round(alg / (ms / 1e3) / 1e9 / peak, 4),
+                     "stage_ms": {k: round(v, 3) for k, v in mean.items()}, "params": params}
+        del t, labels
+        torch.cuda.empty_cache()
     return out
 
 
@@ -353,7 +462,10 @@ def main():
     ap.add_argument("--cpu-frac", type=float, default=0.125)
     ap.add_argument("--ref-frac", type=float, default=0.0625)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--served-requests", type=int, default=120)
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--configs", default="fof-uniform-32K,fof-clumps-16M,dbscan-blobs-10M,fof-halos-16M",
+                    help="the other workloads reported beside the headline one (one short run each)")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--params", default="",
@@ -467,6 +579,17 @@ def main():
             "frac": round(achieved / peak, 4), "traffic": None if traffic_pp is None else int(traffic_pp * n),
             "algorithmic_bytes": int(alg), "peak_source": peak_kind,
             "frac_of_nominal_7900": round(achieved / 7900.0, 4)}
+    # the pair traversal on its own (candidate pass + union pass), on the
+    # contract's per-point model: own point 16 + nodes and leaves touched
+    # once 48 + parent read-modify-write 8 = 72 B/point
+    trav_ms = mean_ms.get("candidates", 0.0) + mean_ms.get("union", 0.0)
+    trav_alg = TRAVERSAL_BYTES_PER_POINT * n
+    trav_gbs = trav_alg / (trav_ms / 1e3) / 1e9 if trav_ms > 0 else 0.0
+    traversal = {"bound": "hbm", "kernels": "k_cand + k_union", "ms": round(trav_ms, 3),
+                 "algorithmic_bytes": int(trav_alg), "bytes_per_point": TRAVERSAL_BYTES_PER_POINT,
+                 "achieved": round(trav_gbs, 1), "peak": peak, "unit": "GB/s",
+                 "frac": round(trav_gbs / peak, 4), "peak_source": peak_kind}
+    roof["traversal"] = traversal
     total_alg = sum(stage_bytes(k, counters, n) for k in names) * n
     pipeline = {"algorithmic_bytes_per_point": round(total_alg / n, 1),
                 "achieved_gbs": round(total_alg / (ms_step / 1e3) / 1e9, 1),
@@ -483,12 +606,22 @@ def main():
             "stage_ms": {k: round(v, 3) for k, v in mean_ms.items()}, "counters": counters,
             "params": tuned if tuned is not None else "library defaults",
             "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_configs:
+        line["configs"] = other_configs(abx, args.configs.split(","))
     if rank == 0 and ws == 1 and not args.no_served:
         del t, labels
         torch.cuda.synchronize()
-        line["served"] = served_benchmark(abx, args.served_requests, 200.0, device=True,
-                                          cpu_baseline=not args.no_cpu_baseline)
-        line["served_host"] = served_benchmark(abx, args.served_requests, 200.0, device=False)
+        rp = RequestPoints(args.served_requests, 200.0)
+        try:
+            dall = torch.from_numpy(rp.all).cuda()
+            picks = tune_batches(abx, rp, dall)
+            line["served"] = served_benchmark(abx, args.served_requests, 200.0, device=True,
+                                              cpu_baseline=not args.no_cpu_baseline, rp=rp, dall=dall,
+                                              tuned=picks)
+            line["served_host"] = served_benchmark(abx, args.served_requests, 200.0, device=False, rp=rp)
+            del dall
+        finally:
+            rp.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, p, args.cpu_frac)
     if rank == 0:

@@ -81,6 +81,13 @@ typedef struct CUstream_st *abx_stream;
  *   block        threads per block of the traversal kernels (64..1024, default 256)
  *   dense_min    a cell is dense only with at least max(minPts, 2, dense_min)
  *                points (0..1<<20, default 0)
+ *   schedule     how the pair traversal (paper, subsection "Pair traversal") is
+ *                scheduled: 1 = two passes, one rope walk per leaf with the
+ *                leaf's box collecting candidate leaves, then one thread per
+ *                point testing them (the default); 2 = one pass, every point
+ *                walks the ropes from its own leaf with its own box
+ *   sort_digit_bits  bits per radix-sort digit (8, 10 or 11; default 8): wider
+ *                digits take fewer passes over the keys
  */
 typedef struct abx_params {
     int32_t leaf_size;
@@ -88,7 +95,9 @@ typedef struct abx_params {
     int32_t sub_bits;
     int32_t block;
     int32_t dense_min;
-    int32_t reserved[3];
+    int32_t schedule;
+    int32_t sort_digit_bits;
+    int32_t reserved[1];
 } abx_params;
 
 /* Human-readable name of a status code (static storage). */
@@ -138,8 +147,8 @@ abx_status abx_dbscan_host(const float *points_host, int64_t n, float eps, int32
  * abx_graph_launch enqueues one replay on `stream` (ABX_EINVAL if the current
  * device is not the one the graph was made on); replays on different streams
  * share the workspace, so keep them in order on one stream.
- * abx_graph_destroy waits for the device, then frees the graph and its
- * workspace.
+ * abx_graph_destroy waits for the graph's last replay (not for other work on
+ * the device), then frees the graph and its workspace.
  */
 typedef struct abx_graph abx_graph;
 abx_status abx_graph_create(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
@@ -174,6 +183,14 @@ abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t
                             const float *eps, const int32_t *minpts, int32_t *labels,
                             abx_stream stream);
 
+/* abx_dbscan_batch with explicit tuning parameters.  params NULL: the
+ * parameters abx_autotune_batch remembered for batches of this class (total
+ * points, any DBSCAN segment or none), else the library defaults; the serving
+ * loop's batches take this path. */
+abx_status abx_dbscan_batch_ex(const float *points, const int64_t *offsets, int32_t nseg,
+                               const float *eps, const int32_t *minpts, int32_t *labels,
+                               const abx_params *params, abx_stream stream);
+
 /*
  * abx_dbscan_noalloc -- abx_dbscan for callers that cannot allocate device
  * memory (an in-situ hook inside a simulation that has reserved the GPU's
@@ -189,11 +206,24 @@ abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t
  * address and sets kernel attributes; make that first call before any stream
  * capture.  Every call on a device shares the array: calls whose work
  * overlaps on the GPU race, so serialise them (one stream, one at a time).
- * Device-side error flags of this entry point are kept apart and are not
- * reported by abx_device_status: pass finite coordinates.
+ * Device-side errors of this entry point (a non-finite coordinate, a bounded
+ * wait that ran out) go to a status word of its own in the same fixed device
+ * memory; abx_device_status reads and clears it together with the library's.
  */
 abx_status abx_dbscan_noalloc(const float *points, int64_t n, float eps, int32_t minpts,
                               int32_t *labels, abx_stream stream);
+
+/*
+ * abx_selftest_wait_timeout -- check that a device wait that can never be
+ * satisfied gives up instead of hanging: one thread runs the library's
+ * bounded look-back wait (the one the radix sort and the scans use) over a
+ * status array in which no predecessor ever publishes, re-reading it at most
+ * spin_limit (1 .. 2^24) times, then records a timeout in the device status
+ * word and returns.  Enqueued on `stream`; a following abx_device_status
+ * returns ABX_ETIMEOUT (and clears it).  No GPU fault, no trap.  The paper
+ * has no counterpart: this is failure detection for the library itself.
+ */
+abx_status abx_selftest_wait_timeout(int32_t spin_limit, abx_stream stream);
 
 /* ---- per-cluster statistics --------------------------------------------------- */
 
@@ -218,14 +248,24 @@ abx_status abx_cluster_stats(const float *points, const int32_t *labels, int64_t
 /*
  * abx_autotune -- time candidate parameters on this input (leaf size, then
  * traversal block size, then dense cells on/off and the minimum dense-cell
- * size, keeping the best so far; each candidate once to warm up and twice
- * timed with CUDA events on `stream`), remember the fastest for this device and
- * size class (friends-of-friends or DBSCAN, floor(log2 n)), and return it in
- * *best (may be NULL).  Later abx_dbscan calls of that class without explicit
- * parameters use it.  labels (device int32 [n]) receives the labels.  Blocks.
+ * size, then the traversal schedule, keeping the best so far; each candidate
+ * once to warm up and twice timed with CUDA events on `stream`), remember the
+ * fastest for this device and size class (friends-of-friends or DBSCAN,
+ * floor(log2 n)), and return it in *best (may be NULL).  Later abx_dbscan
+ * calls of that class without explicit parameters use it.  labels (device
+ * int32 [n]) receives the labels.  Blocks.
  */
 abx_status abx_autotune(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
                         abx_params *best, abx_stream stream);
+
+/*
+ * abx_autotune_batch -- the same search on a batch (arguments as for
+ * abx_dbscan_batch), remembered for batches of its class (total points, any
+ * DBSCAN segment or none) and used by later abx_dbscan_batch calls and by the
+ * serving loop.  Blocks.
+ */
+abx_status abx_autotune_batch(const float *points, const int64_t *offsets, int32_t nseg, const float *eps,
+                              const int32_t *minpts, int32_t *labels, abx_params *best, abx_stream stream);
 
 /* The remembered parameters of the size class of (n, minpts) on the current
  * device (ABX_EINVAL if none), and setting them (e.g. from a saved table). */
@@ -319,12 +359,15 @@ abx_status abx_serve_create(const abx_serve_config *cfg, abx_server **out);
  * labels: int32 [n], both caller-owned, both host memory or both device
  * memory of the server's device (device-resident requests, the in-situ case,
  * skip the host staging), left untouched by the caller until abx_serve_wait
- * returns for the ticket.  Returns at once with a ticket;
+ * returns for the ticket.  producer: for device requests, the stream whose
+ * work writes the points (NULL = legacy default stream); the server reads
+ * them only after everything enqueued on it at the time of the call.  Host
+ * points must be complete when the call is made.  Returns at once with a ticket;
  * ABX_ENOMEM_BUDGET if the request alone exceeds the budget or the batch
  * size, ABX_EBUSY if the queue is full, ABX_EINVAL for bad arguments.
  */
 abx_status abx_serve_submit(abx_server *srv, const float *points, int64_t n, float eps, int32_t minpts,
-                            int32_t *labels, uint64_t *ticket);
+                            int32_t *labels, abx_stream producer, uint64_t *ticket);
 
 /*
  * abx_serve_wait -- wait up to timeout_ms (< 0: forever) for a request:
@@ -356,9 +399,11 @@ typedef struct abx_bvh abx_bvh;
  * the library copies what it needs, so points may be freed once the stream
  * has passed the call.  *out receives the handle; the build is enqueued on
  * `stream` and the handle may be used on that stream right away.
- * leaf_size as in abx_params (0 = default).  1 <= n <= 2^31 - 1.
+ * params: NULL or tuning parameters as for abx_dbscan_ex (leaf_size and
+ * sort_digit_bits apply; dense cells are never built here).
+ * 1 <= n <= 2^31 - 1; ABX_EINVAL for bad parameters.
  */
-abx_status abx_bvh_build(const float *points, int64_t n, int32_t leaf_size, abx_bvh **out,
+abx_status abx_bvh_build(const float *points, int64_t n, const abx_params *params, abx_bvh **out,
                          abx_stream stream);
 
 /*
@@ -395,6 +440,32 @@ abx_status abx_bvh_first_hit(const abx_bvh *bvh, const float *queries, int64_t n
  */
 abx_status abx_bvh_pair_histogram(const abx_bvh *bvh, const float *r_edges, int32_t nbins, uint64_t *hist,
                                   abx_stream stream);
+
+/*
+ * abx_bvh_pairs -- every unordered pair {i, j} of the hierarchy's points with
+ * pred(i, j) for this eps, each exactly once, handed to the caller: the
+ * generic "find all pairs within a radius, apply F" form of the paper's pair
+ * traversal (subsections "Pair traversal" and "Callbacks"; the library cannot
+ * run a caller's function on the device, so the caller applies F to the
+ * pairs).  Pairs are written as pairs[2k] < pairs[2k + 1], original indices
+ * (positions in the points given to abx_bvh_build), in a fixed order:
+ * point by point in the hierarchy's internal order, then in traversal order.
+ * Resumable: *cursor (0 to start) is a position in that internal order; each
+ * call writes the pairs of as many following points as fit in cap pairs,
+ * sets *n_written to their number and advances *cursor; *cursor == n means
+ * all pairs were delivered.
+ *   eps       finite, >= 0
+ *   cursor    host, in/out, 0 <= *cursor <= n
+ *   pairs     device int32 [cap][2] (may be NULL when cap = 0)
+ *   cap       pairs the buffer holds, >= 0
+ *   n_written host, out
+ * ABX_ENOMEM (nothing written, cursor unchanged) if the next point alone has
+ * more than cap pairs: call again with a larger buffer.  Each call counts the
+ * pairs of all remaining points once more, so larger buffers mean fewer
+ * passes.  Waits for `stream`.
+ */
+abx_status abx_bvh_pairs(const abx_bvh *bvh, float eps, int64_t *cursor, int32_t *pairs, int64_t cap,
+                         int64_t *n_written, abx_stream stream);
 
 /* Number of points, leaves and levels (depth of the deepest leaf + 1) of a
  * built hierarchy; waits for `stream`. */

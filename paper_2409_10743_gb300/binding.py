@@ -31,7 +31,10 @@ class Params(ctypes.Structure):
     """abx_params: 0 in any field = library default; no field changes the labels."""
     _fields_ = [("leaf_size", ctypes.c_int32), ("dense_cells", ctypes.c_int32),
                 ("sub_bits", ctypes.c_int32), ("block", ctypes.c_int32), ("dense_min", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("schedule", ctypes.c_int32), ("sort_digit_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+
+
+PARAM_KEYS = ("leaf_size", "dense_cells", "sub_bits", "block", "dense_min", "schedule", "sort_digit_bits")
 
 
 class ServeConfig(ctypes.Structure):
@@ -62,8 +65,11 @@ _SIGS = {
     "abx_graph_launch": (_i32, [_vp, _vp]),
     "abx_graph_destroy": (_i32, [_vp]),
     "abx_device_status": (_i32, [_vp]),
+    "abx_selftest_wait_timeout": (_i32, [_i32, _vp]),
     "abx_dbscan_batch": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
-    "abx_bvh_build": (_i32, [_vp, _i64, _i32, ctypes.POINTER(_vp), _vp]),
+    "abx_dbscan_batch_ex": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, ctypes.POINTER(Params), _vp]),
+    "abx_autotune_batch": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, ctypes.POINTER(Params), _vp]),
+    "abx_bvh_build": (_i32, [_vp, _i64, ctypes.POINTER(Params), ctypes.POINTER(_vp), _vp]),
     "abx_bvh_count": (_i32, [_vp, _vp, _i64, _f32, _i32, _vp, _vp]),
     "abx_bvh_first_hit": (_i32, [_vp, _vp, _i64, _f32, _vp, _vp]),
     "abx_bvh_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32), _vp]),
@@ -77,11 +83,12 @@ _SIGS = {
     "abx_profile_traversal": (_i32, [_vp, _i32]),
     "abx_cluster_stats": (_i32, [_vp, _vp, _i64, ctypes.POINTER(_i32), _vp, _vp, _vp, _vp, _vp]),
     "abx_bvh_pair_histogram": (_i32, [_vp, _vp, _i32, _vp, _vp]),
+    "abx_bvh_pairs": (_i32, [_vp, _f32, ctypes.POINTER(_i64), _vp, _i64, ctypes.POINTER(_i64), _vp]),
     "abx_autotune": (_i32, [_vp, _i64, _f32, _i32, _vp, ctypes.POINTER(Params), _vp]),
     "abx_tune_get": (_i32, [_i64, _i32, ctypes.POINTER(Params)]),
     "abx_tune_set": (_i32, [_i64, _i32, ctypes.POINTER(Params)]),
     "abx_serve_create": (_i32, [ctypes.POINTER(ServeConfig), ctypes.POINTER(_vp)]),
-    "abx_serve_submit": (_i32, [_vp, _vp, _i64, _f32, _i32, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "abx_serve_submit": (_i32, [_vp, _vp, _i64, _f32, _i32, _vp, _vp, ctypes.POINTER(ctypes.c_uint64)]),
     "abx_serve_wait": (_i32, [_vp, ctypes.c_uint64, _i32]),
     "abx_serve_stats": (_i32, [_vp, ctypes.POINTER(ServeReport)]),
     "abx_serve_destroy": (_i32, [_vp]),
@@ -198,21 +205,41 @@ def dbscan_host(points: np.ndarray, eps: float, minpts: int, labels: np.ndarray 
     return labels
 
 
-def dbscan_batch(points, offsets, eps, minpts, labels=None, stream=None):
-    """Cluster concatenated segments; labels are segment-local."""
-    import torch
-    p = _points_dev(points)
+def _segments(offsets, eps, minpts):
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     nseg = off.size - 1
     e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float32), (nseg,)), dtype=np.float32)
     m = np.ascontiguousarray(np.broadcast_to(np.asarray(minpts, np.int32), (nseg,)), dtype=np.int32)
+    return off, nseg, e, m
+
+
+def dbscan_batch(points, offsets, eps, minpts, labels=None, params: Params | None = None, stream=None):
+    """Cluster concatenated segments; labels are segment-local."""
+    import torch
+    p = _points_dev(points)
+    off, nseg, e, m = _segments(offsets, eps, minpts)
     if labels is None:
         labels = torch.empty(p.shape[0], dtype=torch.int32, device=p.device)
     with torch.cuda.device(p.device):
-        rc = lib().abx_dbscan_batch(p.data_ptr(), off.ctypes.data, nseg, e.ctypes.data, m.ctypes.data,
-                                    labels.data_ptr(), _stream(stream))
+        rc = lib().abx_dbscan_batch_ex(p.data_ptr(), off.ctypes.data, nseg, e.ctypes.data, m.ctypes.data,
+                                       labels.data_ptr(), ctypes.byref(params) if params is not None else None,
+                                       _stream(stream))
     _check(rc, "abx_dbscan_batch")
     return labels
+
+
+def autotune_batch(points, offsets, eps, minpts, stream=None) -> dict:
+    """Time candidate parameters on this batch; the winner is remembered for
+    batches of its class (used by dbscan_batch and the server) and returned."""
+    import torch
+    p = _points_dev(points)
+    off, nseg, e, m = _segments(offsets, eps, minpts)
+    lab = torch.empty(p.shape[0], dtype=torch.int32, device=p.device)
+    best = Params()
+    rc = lib().abx_autotune_batch(p.data_ptr(), off.ctypes.data, nseg, e.ctypes.data, m.ctypes.data,
+                                  lab.data_ptr(), ctypes.byref(best), _stream(stream))
+    _check(rc, "abx_autotune_batch")
+    return {k: getattr(best, k) for k in PARAM_KEYS}
 
 
 def autotune(points, eps: float, minpts: int, stream=None) -> dict:
@@ -225,13 +252,13 @@ def autotune(points, eps: float, minpts: int, stream=None) -> dict:
     rc = lib().abx_autotune(p.data_ptr(), p.shape[0], float(np.float32(eps)), int(minpts), lab.data_ptr(),
                             ctypes.byref(best), _stream(stream))
     _check(rc, "abx_autotune")
-    return {k: getattr(best, k) for k in ("leaf_size", "dense_cells", "sub_bits", "block", "dense_min")}
+    return {k: getattr(best, k) for k in PARAM_KEYS}
 
 
 def tune_get(n: int, minpts: int):
     p = Params()
     return None if lib().abx_tune_get(int(n), int(minpts), ctypes.byref(p)) != ABX_OK else \
-        {k: getattr(p, k) for k in ("leaf_size", "dense_cells", "sub_bits", "block", "dense_min")}
+        {k: getattr(p, k) for k in PARAM_KEYS}
 
 
 def tune_set(n: int, minpts: int, params: dict) -> None:
@@ -304,12 +331,15 @@ class BVH:
     """abx_bvh handle: build over device points, early-terminated counts and
     first hits, pair-distance histograms."""
 
-    def __init__(self, points, leaf_size: int = 0, stream=None):
+    def __init__(self, points, leaf_size: int = 0, stream=None, params: Params | None = None):
         p = _points_dev(points)
         self._h = ctypes.c_void_p()
         self._stream = _stream(stream)
         self._points = p  # the build reads the points asynchronously
-        rc = lib().abx_bvh_build(p.data_ptr(), p.shape[0], int(leaf_size), ctypes.byref(self._h), self._stream)
+        if params is None:
+            params = Params(leaf_size=int(leaf_size))
+        rc = lib().abx_bvh_build(p.data_ptr(), p.shape[0], ctypes.byref(params), ctypes.byref(self._h),
+                                 self._stream)
         _check(rc, "abx_bvh_build")
 
     def count(self, queries, eps: float, cap: int, out=None):
@@ -343,6 +373,31 @@ class BVH:
         _check(rc, "abx_bvh_pair_histogram")
         return h
 
+    def pairs_chunk(self, eps: float, cursor: int, out):
+        """One call of abx_bvh_pairs: (status, new cursor, pairs written) into
+        out, a CUDA int32 tensor of shape (cap, 2)."""
+        cur = ctypes.c_int64(int(cursor))
+        wrote = ctypes.c_int64(0)
+        rc = lib().abx_bvh_pairs(self._h, float(np.float32(eps)), ctypes.byref(cur),
+                                 out.data_ptr() if out.numel() else None, out.shape[0], ctypes.byref(wrote),
+                                 self._stream)
+        return rc, int(cur.value), int(wrote.value)
+
+    def pairs(self, eps: float, cap: int = 1 << 22):
+        """Every unordered neighbour pair once, as an (m, 2) int32 CUDA tensor
+        of original indices with i < j, in the library's fixed order."""
+        import torch
+        out = torch.empty((cap, 2), dtype=torch.int32, device=self._points.device)
+        parts, cursor, n = [], 0, self._points.shape[0]
+        while cursor < n:
+            rc, cursor, wrote = self.pairs_chunk(eps, cursor, out)
+            if rc == ABX_ENOMEM:  # one point has more pairs than the buffer holds
+                out = torch.empty((2 * out.shape[0], 2), dtype=torch.int32, device=out.device)
+                continue
+            _check(rc, "abx_bvh_pairs")
+            parts.append(out[:wrote].clone())
+        return torch.cat(parts) if parts else out[:0].clone()
+
     def info(self):
         n, L, lev = _i64(), _i64(), _i32()
         _check(lib().abx_bvh_info(self._h, ctypes.byref(n), ctypes.byref(L), ctypes.byref(lev), self._stream),
@@ -371,14 +426,18 @@ class Server:
         _check(lib().abx_serve_create(ctypes.byref(c), ctypes.byref(self._h)), "abx_serve_create")
         self._keep = {}
 
-    def submit(self, points, eps: float, minpts: int) -> int:
+    def submit(self, points, eps: float, minpts: int, stream=None) -> int:
         """points: a numpy (n, 3) float32 array (host request) or a CUDA torch
-        tensor (device request); the labels come back on the same side."""
+        tensor (device request); the labels come back on the same side.  For a
+        device request the server reads the points after the work enqueued so
+        far on `stream` (default: torch's current stream), which produced them."""
+        producer = None
         if hasattr(points, "is_cuda") and points.is_cuda:
             import torch
             p = _points_dev(points)
             lab = torch.empty(p.shape[0], dtype=torch.int32, device=p.device)
             pp, lp = p.data_ptr(), lab.data_ptr()
+            producer = _stream(stream)
         else:
             p = np.ascontiguousarray(points, dtype=np.float32)
             if p.ndim != 2 or p.shape[1] != 3:
@@ -386,7 +445,7 @@ class Server:
             lab = np.empty(p.shape[0], dtype=np.int32)
             pp, lp = p.ctypes.data, lab.ctypes.data
         t = ctypes.c_uint64()
-        rc = lib().abx_serve_submit(self._h, pp, p.shape[0], float(np.float32(eps)), int(minpts), lp,
+        rc = lib().abx_serve_submit(self._h, pp, p.shape[0], float(np.float32(eps)), int(minpts), lp, producer,
                                     ctypes.byref(t))
         _check(rc, "abx_serve_submit")
         self._keep[t.value] = (p, lab)

@@ -163,6 +163,196 @@ __global__ void __launch_bounds__(256) k_pair_hist(int64_t n, const State *__res
             atomicAdd(hist + b, (unsigned long long)sh[b]);
 }
 
+// ---- every pair within eps, streamed to the caller ------------------------------------
+// The generic form of the paper's pair traversal ("find all pairs within a
+// radius, apply F", subsection "Pair traversal"; subsection "Callbacks" for
+// the functor interface): the library cannot run a caller's function on the
+// device, so it hands the caller the pairs themselves, each unordered pair
+// once, in a deterministic order, resumable across calls.
+
+// A hierarchy's grid with the neighbour radius of this call (the build used
+// none): e2 and the early-exit margin are recomputed for eps (the margin
+// bound of k_quant: eps_eff * inv_step plus the quantisation's rounding).
+__global__ void k_pairs_prep(const SegState *__restrict__ seg, float eps, SegState *out)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        SegState g = seg[0];
+        g.e2 = __fmul_rn(eps, eps);
+        const double eps_eff = fmax(sqrt((double)g.e2), 0x1p-62) * (1.0 + 0x1p-20);
+        const double mc = ceil(eps_eff * (double)g.inv_step + ldexp(1.0, g.bits - 20));
+        g.margin = (isfinite(mc) && mc < (double)(1 << 22)) ? (int)mc : -1;
+        *out = g;
+    }
+}
+
+// Pair traversal of sorted point i: the points after i in its own leaf, then
+// the leaves after it whose boxes the point's box test cannot rule out,
+// stopping early once the walk leaves a Morton region that holds every cell a
+// neighbour can have.  f(j) for every j with pred(i, j); every unordered pair
+// of the hierarchy's points is met from exactly one of its two ends.
+template <class F>
+__device__ __forceinline__ void pair_walk(int i, const SegState &g, const State *__restrict__ st,
+                                          const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                                          const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
+                                          unsigned *dev_status, F &&f)
+{
+    const int L = st->n_leaves;
+    const float e2 = g.e2;
+    const float4 p = spts[i];
+    const int me = leaf_of[i];
+    const int e_own = leaf_first[me + 1];
+    for (int j = i + 1; j < e_own; j++) {
+        const float4 q = __ldg(spts + j);
+        if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2)
+            f(j, q);
+    }
+    float4 alo, ahi;
+    ld_node(nodes, L - 1 + me, alo, ahi);
+    const int H = reach_level(p.x, p.y, p.z, p.x, p.y, p.z, g);
+    int M = level_of(ahi);
+    int node = region_exit(M, 0, H) ? SENTINEL : __float_as_int(ahi.w);
+    unsigned steps = 0;
+    while (node != SENTINEL) {
+        if ((unsigned)node >= (unsigned)(2 * L - 1) || ++steps > (unsigned)(2 * L)) {
+            atomicOr(dev_status, DEV_INTERNAL);
+            break;
+        }
+        float4 lo, hi;
+        ld_node(nodes, node, lo, hi);
+        if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2) {
+            if (node < L - 1) {
+                node = __float_as_int(lo.w);
+                continue;
+            }
+            const int s = (int)(__float_as_uint(lo.w) & ~DENSE_BIT);
+            const int e = leaf_first[node - (L - 1) + 1];
+            for (int j = s; j < e; j++) {
+                const float4 q = __ldg(spts + j);
+                if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2)
+                    f(j, q);
+            }
+        }
+        const int lv = level_of(hi);
+        if (region_exit(lv, M, H))
+            break;
+        M = max(M, lv);
+        node = __float_as_int(hi.w);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pairs_count(int64_t from, int64_t n, const SegState *__restrict__ g,
+                                                     const State *__restrict__ st, const float4 *__restrict__ spts,
+                                                     const float4 *__restrict__ nodes, const int *__restrict__ leaf_of,
+                                                     const int *__restrict__ leaf_first, int *cnt,
+                                                     unsigned *dev_status)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (from + k >= n)
+        return;
+    int c = 0;
+    pair_walk((int)(from + k), *g, st, spts, nodes, leaf_of, leaf_first, dev_status, [&](int, float4) { c++; });
+    cnt[k] = c;
+}
+
+// Exclusive prefix sums of cnt[0 .. m) into pre[0 .. m] (pre[m] = the total),
+// one pass with a decoupled look-back over tiles of SCAN_TILE counts.
+__global__ void __launch_bounds__(SCAN_THREADS) k_pairs_scan(int64_t m, const int *__restrict__ cnt,
+                                                             long long *pre, unsigned *tile_ctr,
+                                                             unsigned long long *lb, unsigned *dev_status)
+{
+    __shared__ int s_tile;
+    __shared__ unsigned long long s_wsum[SCAN_THREADS / 32];
+    __shared__ unsigned long long s_excl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0)
+        s_tile = (int)atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    const int64_t base = (int64_t)tile * SCAN_TILE + (int64_t)tid * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    unsigned long long mine = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        v[j] = base + j < m ? cnt[base + j] : 0;
+        mine += (unsigned)v[j];
+    }
+    unsigned long long x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(~0u, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        s_wsum[warp] = x;
+    __syncthreads();
+    unsigned long long wpre = 0, total = 0;
+    for (int w = 0; w < SCAN_THREADS / 32; w++) {
+        if (w < warp)
+            wpre += s_wsum[w];
+        total += s_wsum[w];
+    }
+    if (tid == 0) {
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            lb_store(lb, LB_FLAG_PRE | total);
+        } else {
+            lb_store(lb + tile, LB_FLAG_AGG | total);
+            excl = lookback<16>(lb, tile, 1, 0, dev_status);
+            lb_store(lb + tile, LB_FLAG_PRE | (excl + total));
+        }
+        s_excl = excl;
+    }
+    __syncthreads();
+    unsigned long long run = s_excl + wpre + x - mine;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        if (base + j < m)
+            pre[base + j] = (long long)run;
+        run += (unsigned)v[j];
+        if (base + j == m - 1)
+            pre[m] = (long long)run;
+    }
+}
+
+// How many points' pairs fit in cap: the largest k with pre[k] <= cap.
+__global__ void k_pairs_limit(int64_t m, const long long *__restrict__ pre, long long cap, long long *res)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int64_t lo = 0, hi = m;  // pre[0] = 0 <= cap
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= cap)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        res[0] = lo;
+        res[1] = pre[lo];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pairs_emit(int64_t from, const long long *__restrict__ res,
+                                                    const SegState *__restrict__ g, const State *__restrict__ st,
+                                                    const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
+                                                    const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
+                                                    const long long *__restrict__ pre, int32_t *out,
+                                                    unsigned *dev_status)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= res[0])
+        return;
+    const int i = (int)(from + k);
+    const int oi = __float_as_int(spts[i].w);
+    long long w = pre[k];
+    pair_walk(i, *g, st, spts, nodes, leaf_of, leaf_first, dev_status, [&](int, float4 q) {
+        const int oj = __float_as_int(q.w);
+        out[2 * w] = min(oi, oj);
+        out[2 * w + 1] = max(oi, oj);
+        w++;
+    });
+}
+
 }  // namespace abx
 
 extern "C" {
@@ -225,6 +415,59 @@ abx_status abx_cluster_stats(const float *points, const int32_t *labels, int64_t
         return ABX_ECUDA;
     *n_clusters = K;
     return cudaGetLastError() == cudaSuccess ? ABX_OK : ABX_ECUDA;
+}
+
+abx_status abx_bvh_pairs(const abx_bvh *bvh, float eps, int64_t *cursor, int32_t *pairs, int64_t cap,
+                         int64_t *n_written, abx_stream stream)
+{
+    if (!bvh || !cursor || !n_written || cap < 0 || (cap > 0 && !pairs) || !(eps >= 0.0f) ||
+        eps == __builtin_inff())
+        return ABX_EINVAL;
+    const Work &w = bvh->w;
+    const int64_t n = w.n;
+    if (*cursor < 0 || *cursor > n)
+        return ABX_EINVAL;
+    *n_written = 0;
+    const int64_t from = *cursor, m = n - from;
+    if (m == 0)
+        return ABX_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t tiles = (size_t)div_up(m, SCAN_TILE);
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_seg = al(sizeof(SegState)), b_cnt = al((size_t)m * sizeof(int)),
+                 b_pre = al((size_t)(m + 1) * sizeof(long long)), b_lb = al(tiles * sizeof(unsigned long long)),
+                 b_misc = al(4 * sizeof(long long));
+    char *ws = nullptr;
+    if (cudaMallocFromPoolAsync((void **)&ws, b_seg + b_cnt + b_pre + b_lb + b_misc, bvh->pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return ABX_ENOMEM;
+    }
+    SegState *gs = reinterpret_cast<SegState *>(ws);
+    int *cnt = reinterpret_cast<int *>(ws + b_seg);
+    long long *pre = reinterpret_cast<long long *>(ws + b_seg + b_cnt);
+    unsigned long long *lb = reinterpret_cast<unsigned long long *>(ws + b_seg + b_cnt + b_pre);
+    long long *res = reinterpret_cast<long long *>(ws + b_seg + b_cnt + b_pre + b_lb);  // [0..1] result, [2] tickets
+    cudaMemsetAsync(lb, 0, b_lb + b_misc, s);
+    k_pairs_prep<<<1, 32, 0, s>>>(w.seg, eps, gs);
+    k_pairs_count<<<div_up(m, 256), 256, 0, s>>>(from, n, gs, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, cnt,
+                                                 w.dev_status);
+    k_pairs_scan<<<(int)tiles, SCAN_THREADS, 0, s>>>(m, cnt, pre, reinterpret_cast<unsigned *>(res + 2), lb,
+                                                     w.dev_status);
+    k_pairs_limit<<<1, 32, 0, s>>>(m, pre, (long long)cap, res);
+    k_pairs_emit<<<div_up(m, 256), 256, 0, s>>>(from, res, gs, w.st, w.spts, w.nodes, w.leaf_of, w.leaf_first, pre,
+                                                pairs, w.dev_status);
+    note_launch(5);
+    long long host[2] = {0, 0}, first_need = 0;
+    cudaMemcpyAsync(host, res, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&first_need, pre + 1, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(ws, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return ABX_ECUDA;
+    if (host[0] == 0)
+        return first_need > cap ? ABX_ENOMEM : ABX_OK;  // the next point's pairs alone do not fit
+    *cursor = from + host[0];
+    *n_written = host[1];
+    return ABX_OK;
 }
 
 abx_status abx_bvh_pair_histogram(const abx_bvh *bvh, const float *r_edges, int32_t nbins, uint64_t *hist,

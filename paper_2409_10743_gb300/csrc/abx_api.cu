@@ -47,6 +47,7 @@ static abx_status device_ctx(DeviceCtx **out)
             return ABX_ECUDA;
         kernels_init_device();
         tree_init_device();
+        cluster_init_device();
         if (cudaGetLastError() != cudaSuccess)
             return ABX_ECUDA;
         c.ready = true;
@@ -152,7 +153,7 @@ static void carve(Carver &c, Work &w, int64_t n, int nseg)
     w.keys[1] = c.take<unsigned long long>(N);
     w.vals[0] = c.take<unsigned>(N);
     w.vals[1] = c.take<unsigned>(N);
-    w.sort_lb = c.take<unsigned long long>((size_t)MAX_PASSES * w.sort_tiles * RADIX);
+    w.sort_lb = c.take<unsigned long long>((size_t)(MAX_PASSES + 1) * w.sort_tiles * RADIX);
     w.scan_lb = c.take<unsigned long long>(w.scan_tiles);
     w.spts = c.take<float4>(N);
     w.dense_root = c.take<int>(N);
@@ -161,6 +162,7 @@ static void carve(Carver &c, Work &w, int64_t n, int nseg)
     w.pdelta = c.take<unsigned char>(N);
     w.delta = c.take<unsigned char>(N);
     w.nodes = c.take<float4>(2 * (2 * N - 1));
+    w.bpts = w.nodes;  // 2 (2n - 1) >= n records
     w.slot = c.take<unsigned long long>(N);
     w.frontier = c.take<int4>(N);
     w.cand = w.frontier;
@@ -194,8 +196,20 @@ abx_status resolve_params(const abx_params *in, Params &p)
     p.sub_bits = 0;
     p.block = 256;
     p.dense_min = 0;
+    p.schedule = 1;
+    p.digit_bits = 8;
     if (!in)
         return ABX_OK;
+    if (in->schedule) {
+        if (in->schedule != 1 && in->schedule != 2)
+            return ABX_EINVAL;
+        p.schedule = in->schedule;
+    }
+    if (in->sort_digit_bits) {
+        if (in->sort_digit_bits != 8 && in->sort_digit_bits != 10 && in->sort_digit_bits != 11)
+            return ABX_EINVAL;
+        p.digit_bits = in->sort_digit_bits;
+    }
     if (in->dense_min) {
         if (in->dense_min < 0 || in->dense_min > (1 << 20))
             return ABX_EINVAL;
@@ -250,6 +264,16 @@ static void run_stages(Work &w, const float *points, int32_t *labels, const Para
         if (g_prof_state)
             cudaMemcpyAsync(g_prof_state, w.st, sizeof(State), cudaMemcpyDeviceToHost, s);
     }
+}
+
+// Self-test of the bounded device waits: the look-back of the radix sort and
+// the flag scan, run by one thread for tile `tile` over a status array whose
+// words are all unpublished, so the wait can only run out.
+__global__ void k_selftest_lookback(const unsigned long long *lb, int tile, int spin_limit, unsigned *dev_status,
+                                    unsigned long long *out)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *out = lookback<8>(lb, tile, 1, 0, dev_status, spin_limit);
 }
 
 }  // namespace abx
@@ -347,11 +371,14 @@ struct abx_graph {
     void *ws = nullptr;           // the graph's own workspace (cudaMalloc)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t last = nullptr;   // recorded after every replay
     unsigned long long launches = 0;  // kernels per replay
 };
 
 static void graph_free(abx_graph *g)
 {
+    if (g->last)
+        cudaEventDestroy(g->last);
     if (g->exec)
         cudaGraphExecDestroy(g->exec);
     if (g->graph)
@@ -411,6 +438,8 @@ abx_status abx_graph_create(const float *points, int64_t n, float eps, int32_t m
     g->launches = t_launches - l0;
     if (e == cudaSuccess)
         e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&g->last, cudaEventDisableTiming);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -428,7 +457,8 @@ abx_status abx_graph_launch(abx_graph *g, abx_stream stream)
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device)
         return ABX_EINVAL;
-    if (cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    if (cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess ||
+        cudaEventRecord(g->last, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) {
         cudaGetLastError();
         return ABX_ECUDA;
     }
@@ -445,7 +475,11 @@ abx_status abx_graph_destroy(abx_graph *g)
     cudaGetDevice(&cur);
     if (cur != dev)
         cudaSetDevice(dev);
-    cudaDeviceSynchronize();  // no replay may still read the workspace
+    // no replay may still use the workspace: replays are kept in order on one
+    // stream, so waiting for the last one's event is enough (other work on
+    // the device is not waited for)
+    if (g->last)
+        cudaEventSynchronize(g->last);
     graph_free(g);
     if (cur >= 0 && cur != dev)
         cudaSetDevice(cur);
@@ -492,11 +526,14 @@ abx_status abx_device_status(abx_stream stream)
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return ABX_ECUDA;
-    unsigned v = 0;
+    unsigned v = 0, v_noalloc = 0;
     if (cudaMemcpy(&v, ctx->status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
         return ABX_ECUDA;
     if (v && cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess)
         return ABX_ECUDA;
+    if (noalloc_take_status(&v_noalloc) != ABX_OK)
+        return ABX_ECUDA;
+    v |= v_noalloc;
     if (v & DEV_INTERNAL)
         return ABX_EINTERNAL;
     if (v & DEV_TIMEOUT)
@@ -504,6 +541,29 @@ abx_status abx_device_status(abx_stream stream)
     if (v & DEV_NONFINITE)
         return ABX_ENONFINITE;
     return ABX_OK;
+}
+
+abx_status abx_selftest_wait_timeout(int32_t spin_limit, abx_stream stream)
+{
+    if (spin_limit < 1 || spin_limit > (1 << 24))
+        return ABX_EINVAL;
+    DeviceCtx *ctx;
+    abx_status rc = device_ctx(&ctx);
+    if (rc != ABX_OK)
+        return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    constexpr int TILES = 4;
+    unsigned long long *lb = nullptr;
+    if (cudaMallocFromPoolAsync((void **)&lb, (TILES + 1) * sizeof(unsigned long long), ctx->pool, s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return ABX_ENOMEM;
+    }
+    cudaMemsetAsync(lb, 0, (TILES + 1) * sizeof(unsigned long long), s);  // nothing published
+    k_selftest_lookback<<<1, 32, 0, s>>>(lb, TILES - 1, spin_limit, ctx->status, lb + TILES);
+    note_launch();
+    cudaFreeAsync(lb, s);
+    return cuda_status(cudaGetLastError());
 }
 
 static const char *k_stage_names[ST_NUM] = {"bounds", "morton", "sort", "gather", "cells", "leaves",
@@ -579,6 +639,12 @@ abx_status abx_profile_counters(int64_t *out, int32_t n)
 abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t nseg, const float *eps,
                             const int32_t *minpts, int32_t *labels, abx_stream stream)
 {
+    return abx_dbscan_batch_ex(points, offsets, nseg, eps, minpts, labels, nullptr, stream);
+}
+
+abx_status abx_dbscan_batch_ex(const float *points, const int64_t *offsets, int32_t nseg, const float *eps,
+                               const int32_t *minpts, int32_t *labels, const abx_params *params, abx_stream stream)
+{
     if (nseg < 0 || (nseg > 0 && (!offsets || !eps || !minpts)))
         return ABX_EINVAL;
     if (nseg == 0)
@@ -597,8 +663,17 @@ abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t
         return ABX_EINVAL;
     if (n == 0)
         return ABX_OK;
+    bool any_dbscan = false;
+    for (int32_t k = 0; k < nseg; k++)
+        any_dbscan |= minpts[k] > 2;
+    abx_params tuned;
+    if (!params && tune_lookup_batch(n, any_dbscan, &tuned))
+        params = &tuned;  // the autotuner's choice for batches of this class
+    Params p;
+    if (resolve_params(params, p) != ABX_OK)
+        return ABX_EINVAL;
     if (nseg == 1)
-        return abx_dbscan(points, n, eps[0], minpts[0], labels, stream);
+        return abx_dbscan_ex(points, n, eps[0], minpts[0], labels, params, stream);
     DeviceCtx *ctx;
     abx_status rc = device_ctx(&ctx);
     if (rc != ABX_OK)
@@ -613,23 +688,25 @@ abx_status abx_dbscan_batch(const float *points, const int64_t *offsets, int32_t
     work_carve(w, ws, n, nseg);
     w.n_sms = ctx->n_sms;
     w.dev_status = ctx->status;
-    // segment table: int32 offsets, eps, minPts (host arrays are read before
-    // this call returns: the copies are from pageable memory)
+    // segment table: int32 offsets, eps, minPts, staged in local (pageable)
+    // copies, so the caller's host arrays -- pinned or not -- are read before
+    // this call returns (a copy from pageable memory has consumed its source
+    // when cudaMemcpyAsync returns)
     std::vector<int> off32((size_t)nseg + 1);
     for (int32_t k = 0; k <= nseg; k++)
         off32[k] = (int)offsets[k];
+    std::vector<float> eps_v(eps, eps + nseg);
+    std::vector<int> minpts_v(minpts, minpts + nseg);
     for (int32_t k = 0; k < nseg; k++) {
         w.any_fof |= minpts[k] <= 2;
         w.any_dbscan |= minpts[k] > 2;
     }
     cudaMemcpyAsync(w.seg_off, off32.data(), off32.size() * sizeof(int), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(w.seg_eps_in, eps, (size_t)nseg * sizeof(float), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(w.seg_minpts_in, minpts, (size_t)nseg * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(w.seg_eps_in, eps_v.data(), (size_t)nseg * sizeof(float), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(w.seg_minpts_in, minpts_v.data(), (size_t)nseg * sizeof(int), cudaMemcpyHostToDevice, s);
     int seg_bits = 0;
     while ((1ll << seg_bits) < (long long)nseg)
         seg_bits++;
-    Params p;
-    resolve_params(nullptr, p);
     prof_begin(s);
     stage_segments_batch(w, w.seg_eps_in, w.seg_minpts_in, seg_bits, s);
     run_stages(w, points, labels, p, s);

@@ -115,10 +115,15 @@ __global__ void k_levels(const State *__restrict__ st, const float4 *__restrict_
 
 extern "C" {
 
-abx_status abx_bvh_build(const float *points, int64_t n, int32_t leaf_size, abx_bvh **out, abx_stream stream)
+abx_status abx_bvh_build(const float *points, int64_t n, const abx_params *params, abx_bvh **out,
+                         abx_stream stream)
 {
-    if (!out || !points || n < 1 || n > INT32_MAX || leaf_size < 0 || leaf_size > 32)
+    if (!out || !points || n < 1 || n > INT32_MAX)
         return ABX_EINVAL;
+    Params p;
+    if (resolve_params(params, p) != ABX_OK)
+        return ABX_EINVAL;
+    p.dense = 0;  // no eps here: the grid only resolves the points
     cudaMemPool_t pool;
     unsigned *status;
     int n_sms;
@@ -137,7 +142,6 @@ abx_status abx_bvh_build(const float *points, int64_t n, int32_t leaf_size, abx_
     work_carve(h->w, h->ws, n);
     h->w.n_sms = n_sms;
     h->w.dev_status = status;
-    Params p{leaf_size ? leaf_size : 4, 0, 0, 256, 0};
     h->w.any_fof = true;
     stage_segments_single(h->w, 0.0f, 2, s);
     stage_bounds_quant(h->w, points, p, s);

@@ -28,6 +28,18 @@ constexpr int sort_items() { return sizeof(K) == 4 ? 32 : 16; }
 template <typename K>
 constexpr int sort_tile() { return SORT_THREADS * sort_items<K>(); }
 constexpr int SORT_TILE_MIN = SORT_THREADS * 16;  // the smaller tile sizes the look-back buffer
+// Below this size the 32-bit key kernels are not launched (their launch costs
+// more than the lighter passes save).
+constexpr int64_t KEY32_MIN_POINTS = 1 << 16;
+// Bucketing pass: above this size the input points no longer fit in L2, and
+// gathering them in key order straight from the input is a random 12-byte
+// read per point over the whole array.  The points are first moved, with
+// their keys, into buckets by the key's top 8 bits (one stable counting pass
+// that reads the input in order); the gather after the sort then reads
+// within one or two buckets at a time, which L2 holds.
+constexpr int64_t BUCKET_MIN_POINTS = 1 << 23;
+constexpr int BUCKET_ROW = MAX_PASSES;          // its histogram row and look-back row
+constexpr int BUCKET_TICKETS = MAX_PASSES + 2;  // its tile counter (tile_ctr index)
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -44,7 +56,7 @@ struct SegState {
     int bits;                   // Morton bits per axis used by this segment
     int dense_ok;               // dense cells usable (cell grid = Morton prefix)
     int root;                   // root of the segment's subtree
-    int pad;
+    int margin;                 // cells a neighbour's quantised coordinate can differ by (-1: unbounded)
 };
 
 // Per-call device state (lives in the call's workspace).
@@ -59,7 +71,9 @@ struct State {
     int n_active;               // radix passes run (the rest are constant digits)
     int pass_ord[MAX_PASSES];   // order of pass p among the active ones, -1 = skipped
     unsigned tile_ctr[MAX_PASSES + 4];
-    unsigned hist[MAX_PASSES][RADIX];   // digit histograms, then exclusive offsets
+    // digit histograms of the radix passes, then exclusive offsets; row
+    // BUCKET_ROW: the same for the bucket digit (the key's top 8 bits)
+    unsigned hist[MAX_PASSES + 1][RADIX];
     int n_cells;                // dense cells found
     int n_leaves;
     int root;                   // root of the whole hierarchy
@@ -105,7 +119,7 @@ __device__ __forceinline__ void lb_store(unsigned long long *p, unsigned long lo
 // with `stride` words per tile, LOOKBACK_WINDOW words per round trip.
 template <int LOOKBACK_WINDOW>
 __device__ __forceinline__ unsigned long long lookback(const unsigned long long *lb, int tile, int stride, int slot,
-                                                       unsigned *dev_status)
+                                                       unsigned *dev_status, int spin_limit = SPIN_LIMIT)
 {
     unsigned long long excl = 0;
     int t = tile - 1;
@@ -127,7 +141,7 @@ __device__ __forceinline__ unsigned long long lookback(const unsigned long long 
         }
         t -= k;
         if (k < LOOKBACK_WINDOW) {
-            if (++spins > SPIN_LIMIT) {
+            if (++spins > spin_limit) {
                 atomicOr(dev_status, DEV_TIMEOUT);
                 return excl;
             }
@@ -151,6 +165,18 @@ __device__ __forceinline__ int seg_of_input(const int *__restrict__ off, int nse
             hi = mid - 1;
     }
     return lo;
+}
+
+// Split level between sorted keys a (position t) and b (position t + 1):
+// 33 + the highest bit in which they differ, or, for equal keys, the level of
+// the (key, position) tie-break, 32 - clz(t ^ (t + 1)) (below every key bit).
+// The hierarchy merges across the lower level first.
+__device__ __forceinline__ unsigned char split_level(unsigned long long a, unsigned long long b, int t)
+{
+    unsigned long long x = a ^ b;
+    if (x)
+        return (unsigned char)(32 + (64 - __clzll((long long)x)));
+    return (unsigned char)(32 - __clz(t ^ (t + 1)));
 }
 
 // Segment of a sorted point, read from the top bits of its key.
@@ -196,6 +222,96 @@ __device__ __forceinline__ float box_box_dist2_rn(float4 alo, float4 ahi, float4
     float dz = fmaxf(0.0f, fmaxf(__fsub_rn(blo.z, ahi.z), __fsub_rn(alo.z, bhi.z)));
     float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
     return __fadd_rn(s, __fmul_rn(dz, dz));
+}
+
+// ---- node records -------------------------------------------------------------
+// One hierarchy record is 32 bytes (lo.xyz + left child or first point, hi.xyz
+// + rope), fetched with a single 256-bit load: one load instruction per node
+// visit instead of two.  Records are read-only in every traversal kernel.
+__device__ __forceinline__ void ld_node(const float4 *nodes, int i, float4 &lo, float4 &hi)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+        : "l"(nodes + 2 * (size_t)i));
+}
+
+// ---- early exit of rope walks (Morton regions) -----------------------------------
+// A coordinate's grid cell, exactly as the Morton kernel quantises it.
+__device__ __forceinline__ unsigned quant_axis(float v, float lo, float inv_step, float qmax)
+{
+    const float t = __fmul_rn(__fsub_rn(v, lo), inv_step);
+    return t < qmax ? (unsigned)fmaxf(t, 0.0f) : (unsigned)qmax;
+}
+
+// The quantisation is monotone, and two points that pass the neighbour test
+// are at most g.margin cells apart on every axis (the margin bounds eps in
+// cells plus the rounding of the quantisation; it is set with the step).  So
+// every neighbour of a point of the box [lo, hi] has its cell in
+// [q(lo) - margin, q(hi) + margin] per axis.  Returned: the highest bit of the
+// interleaved code at which two cells of that grown box can differ (-1: one
+// cell; 255: no bound, the walk never stops early).  Bit 3k + 2 - a holds bit
+// k of axis a.
+__device__ __forceinline__ int reach_level(float lx, float ly, float lz, float hx, float hy, float hz,
+                                           const SegState &g)
+{
+    const int m = g.margin;
+    if (m < 0)
+        return 255;
+    const unsigned qm = (1u << g.bits) - 1u;
+    const float qmax = (float)qm;
+    const float lo3[3] = {lx, ly, lz}, hi3[3] = {hx, hy, hz};
+    int H = -1;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const unsigned ql = quant_axis(lo3[a], g.lo[a], g.inv_step, qmax);
+        const unsigned qh = quant_axis(hi3[a], g.lo[a], g.inv_step, qmax);
+        const unsigned gl = ql > (unsigned)m ? ql - (unsigned)m : 0u;
+        const unsigned gh = qh + (unsigned)m < qm ? qh + (unsigned)m : qm;
+        const unsigned x = gl ^ gh;
+        if (x)
+            H = max(H, 3 * (31 - __clz(x)) + 2 - a);
+    }
+    return H;
+}
+
+// The split level of the leaf boundary a node's rope crosses travels in the
+// lowest 8 bits of the node's hi.x, so a rope walk has it in the record it
+// already loaded.  hi.x is rounded UP to the nearest float with those low
+// bits: the box grows by less than 256 ulps on that side, which keeps every
+// pruning test conservative (a looser box never drops a neighbour).  Near the
+// top of the float range the result may be +inf or a NaN; box_dist2_rn and
+// box_box_dist2_rn then ignore that side (fmaxf returns its other operand),
+// which is conservative too.  Written after the boxes are merged bottom-up.
+__device__ __forceinline__ float with_level(float v, unsigned lv)
+{
+    const unsigned b = __float_as_uint(v);
+    if (!(b >> 31)) {  // +0 or positive: larger bit patterns are larger values
+        unsigned c = (b & ~0xffu) | lv;
+        if (c < b)
+            c += 256u;
+        return __uint_as_float(c);
+    }
+    const unsigned m = b & 0x7fffffffu;  // negative: smaller magnitudes are larger values
+    unsigned c = (m & ~0xffu) | lv;
+    if (c > m) {
+        if (m < 256u)
+            return __uint_as_float(lv);  // +0 or a positive subnormal, above v
+        c -= 256u;
+    }
+    return __uint_as_float(c | 0x80000000u);
+}
+__device__ __forceinline__ int level_of(float4 hi) { return (int)(__float_as_uint(hi.x) & 0xffu); }
+
+// Crossing the leaf boundary whose split level is lv (split_level encoding:
+// lv > 32 is a key split at bit lv - 33; 255 = the end of the walk) while the
+// highest level crossed so far since the walk's own leaf is M: the subtree
+// being left is the left child of that boundary's node, it holds the walk's
+// own leaf iff lv > M, and then it is exactly the set of keys that share the
+// code's bits >= lv - 33.  If the grown box of the query fits in that region
+// (lv - 33 > H), no point after it can be a neighbour: stop.
+__device__ __forceinline__ bool region_exit(int lv, int M, int H)
+{
+    return lv != 255 && lv > M && lv > 32 && lv - 33 > H;
 }
 
 // ---- ordered float <-> int for atomic min/max ---------------------------------

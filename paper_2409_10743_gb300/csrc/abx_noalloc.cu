@@ -58,11 +58,36 @@ static abx_status noalloc_setup(NoAllocDevice **out)
             return ABX_ECUDA;
         kernels_init_device();
         tree_init_device();
+        cluster_init_device();
         if (cudaGetLastError() != cudaSuccess)
             return ABX_ECUDA;
         d.ready = true;
     }
     *out = &d;
+    return ABX_OK;
+}
+
+// The status word of this entry point on the current device, read and
+// cleared (0 if the entry point never ran here).  abx_device_status folds it
+// into the library's status, after waiting for the caller's stream.
+abx_status noalloc_take_status(unsigned *out)
+{
+    *out = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return ABX_ECUDA;
+    unsigned *status = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (g_noalloc_dev[dev].ready)
+            status = g_noalloc_dev[dev].status;
+    }
+    if (!status)
+        return ABX_OK;
+    if (cudaMemcpy(out, status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ABX_ECUDA;
+    if (*out && cudaMemset(status, 0, sizeof(unsigned)) != cudaSuccess)
+        return ABX_ECUDA;
     return ABX_OK;
 }
 
@@ -90,7 +115,8 @@ extern "C" abx_status abx_dbscan_noalloc(const float *points, int64_t n, float e
     w.dev_status = d->status;
     w.any_fof = minpts <= 2;
     w.any_dbscan = !w.any_fof;
-    const Params p{4, 1, 0, 256, 0};
+    Params p;
+    resolve_params(nullptr, p);  // the library defaults
     stage_segments_single(w, eps, minpts, s);
     stage_bounds_quant(w, points, p, s);
     stage_morton_sort(w, points, s);

@@ -47,6 +47,7 @@ struct Request {
     float eps = 0.0f;
     int32_t minpts = 0;
     int32_t *labels = nullptr;
+    cudaEvent_t ready = nullptr;  // device requests: the producer stream at submit
     double t_submit = 0, t_done = 0;
     abx_status status = ABX_OK;
     bool done = false;
@@ -224,7 +225,12 @@ void launch_slot(abx_server *sv, Slot &sl)
         float *dp = static_cast<float *>(d_pts);
         int32_t *dl = static_cast<int32_t *>(d_lab);
         for (int k = 0; k < nseg; k++) {  // gather the batch into one array
-            const Request *r = sl.reqs[k];
+            Request *r = sl.reqs[k];
+            if (r->ready) {  // after everything the producer had enqueued at submit
+                cudaStreamWaitEvent(sl.stream, r->ready, 0);
+                cudaEventDestroy(r->ready);  // released once the event has completed
+                r->ready = nullptr;
+            }
             cudaMemcpyAsync(dp + 3 * sl.off[k], r->on_device ? r->pts : sl.h_pts + 3 * sl.off[k],
                             (size_t)r->n * 3 * sizeof(float),
                             r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sl.stream);
@@ -245,6 +251,11 @@ void launch_slot(abx_server *sv, Slot &sl)
         cudaFreeAsync(d_pts, sl.stream);
     if (d_lab)
         cudaFreeAsync(d_lab, sl.stream);
+    for (Request *r : sl.reqs)  // a batch that failed before its copies
+        if (r->ready) {
+            cudaEventDestroy(r->ready);
+            r->ready = nullptr;
+        }
     if (cudaLaunchHostFunc(sl.stream, on_batch_done, &sl) != cudaSuccess) {
         cudaGetLastError();
         cudaStreamSynchronize(sl.stream);
@@ -375,7 +386,7 @@ abx_status abx_serve_create(const abx_serve_config *cfg, abx_server **out)
 }
 
 abx_status abx_serve_submit(abx_server *sv, const float *points, int64_t n, float eps, int32_t minpts,
-                            int32_t *labels, uint64_t *ticket)
+                            int32_t *labels, abx_stream producer, uint64_t *ticket)
 {
     if (!sv || !ticket || n < 0 || n > INT32_MAX || minpts < 1 || !(eps >= 0.0f) || eps == __builtin_inff() ||
         (n > 0 && (!points || !labels)))
@@ -399,7 +410,20 @@ abx_status abx_serve_submit(abx_server *sv, const float *points, int64_t n, floa
         if (lab_dev != on_device)
             return ABX_EINVAL;  // points and labels must live on the same side
     }
+    cudaEvent_t ready = nullptr;
+    if (on_device) {
+        // the server reads the points on its own streams: order that after
+        // the work the caller's producer stream holds now
+        if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(ready, reinterpret_cast<cudaStream_t>(producer)) != cudaSuccess) {
+            cudaGetLastError();
+            if (ready)
+                cudaEventDestroy(ready);
+            return ABX_ECUDA;
+        }
+    }
     Request *r = new Request();
+    r->ready = ready;
     r->on_device = on_device;
     r->pts = points;
     r->n = n;
@@ -407,13 +431,12 @@ abx_status abx_serve_submit(abx_server *sv, const float *points, int64_t n, floa
     r->minpts = minpts;
     r->labels = labels;
     std::lock_guard<std::mutex> lk(sv->mu);
-    if (sv->stop) {
+    if (sv->stop || (int64_t)sv->pending.size() >= sv->cfg.max_queue) {
+        if (r->ready)
+            cudaEventDestroy(r->ready);
+        const abx_status rc = sv->stop ? ABX_ECANCELLED : ABX_EBUSY;
         delete r;
-        return ABX_ECANCELLED;
-    }
-    if ((int64_t)sv->pending.size() >= sv->cfg.max_queue) {
-        delete r;
-        return ABX_EBUSY;
+        return rc;
     }
     r->ticket = sv->next_ticket++;
     r->t_submit = now_s();
@@ -496,14 +519,21 @@ abx_status abx_serve_destroy(abx_server *sv)
 {
     if (!sv)
         return ABX_EINVAL;
+    std::vector<cudaEvent_t> events;  // released after the lock (no CUDA call under it)
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
         const double t = now_s();
-        for (Request *r : sv->pending)
+        for (Request *r : sv->pending) {
+            if (r->ready)
+                events.push_back(r->ready);
+            r->ready = nullptr;
             finish_request(sv, r, ABX_ECANCELLED, t);
+        }
         sv->pending.clear();
     }
+    for (cudaEvent_t e : events)
+        cudaEventDestroy(e);
     sv->cv_work.notify_all();
     sv->cv_done.notify_all();
     if (sv->th.joinable())

@@ -18,6 +18,8 @@
 // replaced by a separate pass after all unions: each non-core point looks at
 // all its core neighbours and joins the cluster whose smallest core index is
 // smallest.
+#include <algorithm>
+
 #include "work.cuh"
 
 namespace abx {
@@ -26,6 +28,8 @@ struct Tree {
     const float4 *__restrict__ nodes;
     const int *__restrict__ leaf_first;
     int L;
+    const State *st = nullptr;     // with the sorted keys: split levels between any two points
+    const void *k0 = nullptr, *k1 = nullptr;
 };
 
 // A traversal visits every node at most once; a node index outside the
@@ -40,9 +44,6 @@ __device__ __forceinline__ bool node_ok(int node, int L, unsigned &steps, unsign
     return true;
 }
 
-__device__ __forceinline__ float4 node_lo(const Tree &t, int i) { return __ldg(t.nodes + 2 * (size_t)i); }
-__device__ __forceinline__ float4 node_hi(const Tree &t, int i) { return __ldg(t.nodes + 2 * (size_t)i + 1); }
-
 // ---- candidate leaves --------------------------------------------------------------
 // The pair traversal of a point starts at its leaf's rope and descends into
 // every subtree after its leaf that its own box test cannot rule out.  A node
@@ -50,54 +51,125 @@ __device__ __forceinline__ float4 node_hi(const Tree &t, int i) { return __ldg(t
 // every point of the leaf (box_box_dist2_rn is a lower bound of the point's
 // own box distance), so one traversal per leaf with the leaf's box finds the
 // leaves after it that any of its points can reach: its candidate leaves.
-// Each point then tests only the points of those leaves (after its own box
-// test of each) and visits no node.  Up to CAND_K - 1 candidates are kept (one
-// int4 per leaf); when there are more, the last slot holds -(node + 2) for
-// the leaf node where the list ran out, and the points walk the ropes from
-// there on with their own box tests (which visits that leaf and everything
-// after it in pre-order).  -1 ends a list.
+// The walk stops early once the subtree it leaves is a Morton region that
+// holds every cell a neighbour of the leaf can have (region_exit).
+//
+// cand[a] = {end of leaf a's points | DENSE_BIT if leaf a is a dense cell,
+// c0, c1, c2}: up to three candidate leaves, -1 ending the list.  With four or
+// more, c2 = -(node + 2) for the leaf node of the third candidate instead:
+// the points walk the ropes from there on with their own box tests (which
+// visits that leaf and everything after it in pre-order).
 
-constexpr int CAND_K = 4;
+constexpr int CAND_SLOTS = 3;
+constexpr int CAND_TICKETS = MAX_PASSES + 3;  // tile_ctr index of the candidate pass's leaf queue
+static int g_cand_blocks_per_sm = 4;           // set per process by cluster_init_device
 
+// Persistent: the walks differ in length by an order of magnitude, and a warp
+// runs as long as its longest walk, so each lane carries one walk at a time,
+// one node visit per step, and a lane whose walk ended takes the next leaf
+// from the warp's chunk of the leaf queue (chunks of 32 leaves: one global
+// atomic per 32 walks) -- the warp stays full until the queue runs dry.
 template <bool SEG>
-__global__ void k_cand(const State *__restrict__ st, const SegState *__restrict__ seg,
-                       const int *__restrict__ leaf_seg, const float4 *__restrict__ nodes, int4 *cand,
-                       unsigned *dev_status)
+__global__ void __launch_bounds__(256, 6) k_cand(State *__restrict__ st, const SegState *__restrict__ seg,
+                                              const int *__restrict__ leaf_seg, const float4 *__restrict__ nodes,
+                                              const int *__restrict__ leaf_first, int4 *cand, unsigned *dev_status)
 {
     const int L = st->n_leaves;
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= L)
-        return;
-    const Tree T{nodes, nullptr, L};
-    const float e2 = seg[SEG ? leaf_seg[a] : 0].e2;
-    const float4 alo = node_lo(T, L - 1 + a), ahi = node_hi(T, L - 1 + a);
-    int out[CAND_K];
-#pragma unroll
-    for (int k = 0; k < CAND_K; k++)
-        out[k] = SENTINEL;
-    int k = 0;
-    int node = __float_as_int(ahi.w);
+    unsigned *queue = &st->tile_ctr[CAND_TICKETS];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    // this lane's walk
+    int a = 0, node = SENTINEL, M = 0, H = 0, k = 0, own = 0;
+    int out0 = SENTINEL, out1 = SENTINEL, out2 = SENTINEL;
     unsigned steps = 0;
-    while (node != SENTINEL) {
-        if (!node_ok(node, L, steps, dev_status))
-            break;
-        const float4 lo = node_lo(T, node), hi = node_hi(T, node);
-        if (box_box_dist2_rn(alo, ahi, lo, hi) <= e2) {
-            if (node < L - 1) {
-                node = __float_as_int(lo.w);
-                continue;
+    float e2 = 0.0f;
+    float4 alo = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ahi = alo;
+    bool live = false;
+    // the warp's chunk of the queue (the same in every lane)
+    int q_next = 0, q_end = 0;
+    bool dry = false;
+    while (true) {
+        unsigned need = __ballot_sync(~0u, !live);
+        while (need && !dry) {
+            if (q_next >= q_end) {
+                unsigned c = 0;
+                if (lane == 0)
+                    c = atomicAdd(queue, 32u);
+                c = __shfl_sync(~0u, c, 0);
+                if (c >= (unsigned)L) {
+                    dry = true;
+                    break;
+                }
+                q_next = (int)c;
+                q_end = (int)min(c + 32u, (unsigned)L);
             }
-            const int v = k == CAND_K - 1 ? -(node + 2) : node - (L - 1);
-    #pragma unroll
-            for (int q = 0; q < CAND_K; q++)
-                if (q == k)
-                    out[q] = v;
-            if (++k == CAND_K)
-                break;
+            const int avail = q_end - q_next;
+            const int r = __popc(need & lt);
+            if (((need >> lane) & 1u) && r < avail) {
+                a = q_next + r;
+                const SegState &g = seg[SEG ? leaf_seg[a] : 0];
+                e2 = g.e2;
+                ld_node(nodes, L - 1 + a, alo, ahi);
+                own = leaf_first[a + 1] | (int)(__float_as_uint(alo.w) & DENSE_BIT);
+                H = reach_level(alo.x, alo.y, alo.z, ahi.x, ahi.y, ahi.z, g);
+                M = level_of(ahi);  // following the leaf's own rope crosses boundary a
+                node = region_exit(M, 0, H) ? SENTINEL : __float_as_int(ahi.w);
+                k = 0;
+                out0 = out1 = out2 = SENTINEL;
+                steps = 0;
+                live = node != SENTINEL;
+                if (!live)
+                    cand[a] = make_int4(own, SENTINEL, SENTINEL, SENTINEL);
+            }
+            q_next += min(__popc(need), avail);
+            need = __ballot_sync(~0u, !live);
         }
-        node = __float_as_int(hi.w);
+        if (!__any_sync(~0u, live))
+            break;
+        if (!live)
+            continue;
+        // one node visit
+        bool fin = false;
+        if (!node_ok(node, L, steps, dev_status)) {
+            fin = true;
+        } else {
+            float4 lo, hi;
+            ld_node(nodes, node, lo, hi);
+            bool descend = false;
+            if (box_box_dist2_rn(alo, ahi, lo, hi) <= e2) {
+                if (node < L - 1) {
+                    node = __float_as_int(lo.w);
+                    descend = true;
+                } else if (k == CAND_SLOTS) {  // a fourth: resume at the third one's node
+                    out2 = -((L - 1 + out2) + 2);
+                    fin = true;
+                } else {
+                    const int t = node - (L - 1);
+                    if (k == 0)
+                        out0 = t;
+                    else if (k == 1)
+                        out1 = t;
+                    else
+                        out2 = t;
+                    k++;
+                }
+            }
+            if (!descend && !fin) {
+                const int lv = level_of(hi);
+                if (region_exit(lv, M, H)) {
+                    fin = true;
+                } else {
+                    M = max(M, lv);
+                    node = __float_as_int(hi.w);
+                    fin = node == SENTINEL;
+                }
+            }
+        }
+        if (fin) {
+            cand[a] = make_int4(own, out0, out1, out2);
+            live = false;
+        }
     }
-    cand[a] = make_int4(out[0], out[1], out[2], out[3]);
 }
 
 // ---- pair traversal with union-find ------------------------------------------------
@@ -111,22 +183,39 @@ struct TravStats {
     unsigned long long visits, leaves, tests, unions, queries;
 };
 
-template <bool FOF, bool STATS>
-__device__ __forceinline__ void union_query(const int i, const float e2, const Tree &T,
+// SCHED 1: the point tests the candidate leaves its leaf collected (k_cand),
+// then, if the list overflowed, walks the ropes from the leaf where it ran out.
+// SCHED 2: no candidate lists; the point walks the ropes from its own leaf
+// with its own box, stopping early like k_cand (region_exit).
+template <int SCHED, bool FOF, bool STATS>
+__device__ __forceinline__ void union_query(const int i, const SegState &g, const Tree &T,
                                             const float4 *__restrict__ spts, const int *__restrict__ leaf_of,
-                                            const int4 *__restrict__ cand, int *parent, unsigned char *core,
-                                            unsigned *dev_status, TravStats *stats)
+                                            const int4 *__restrict__ cand, int *parent, unsigned char *core, unsigned *dev_status, TravStats *stats)
 {
     const int L = T.L;
+    const float e2 = g.e2;
     const float4 p = spts[i];
     const int *__restrict__ leaf_first = T.leaf_first;
     bool found = false;
     unsigned c_visit = 0, c_leaf = 0, c_test = 0, c_union = 0;
 
-    const int my_leaf = L - 1 + leaf_of[i];
-    const unsigned w0 = __float_as_uint(node_lo(T, my_leaf).w);
-    if (!(w0 & DENSE_BIT)) {
-        const int e = leaf_first[my_leaf - (L - 1) + 1];
+    const int me = leaf_of[i];
+    int own_end;  // end of the own leaf's points, DENSE_BIT set for a dense cell
+    int4 c4 = make_int4(0, SENTINEL, SENTINEL, SENTINEL);
+    int node = SENTINEL, M = 0, H = 255;
+    if (SCHED == 1) {
+        c4 = cand[me];
+        own_end = c4.x;
+    } else {
+        float4 alo, ahi;
+        ld_node(T.nodes, L - 1 + me, alo, ahi);
+        own_end = leaf_first[me + 1] | (int)(__float_as_uint(alo.w) & DENSE_BIT);
+        H = reach_level(p.x, p.y, p.z, p.x, p.y, p.z, g);
+        M = level_of(ahi);
+        node = region_exit(M, 0, H) ? SENTINEL : __float_as_int(ahi.w);
+    }
+    if (own_end >= 0) {  // not a dense cell (its points are one set already)
+        const int e = own_end;
         for (int j = i + 1; j < e; j++) {
             float4 q = __ldg(spts + j);
             if (STATS)
@@ -142,7 +231,7 @@ __device__ __forceinline__ void union_query(const int i, const float e2, const T
             }
         }
     }
-    // the points of leaf [s, e): one of the candidate leaves of i's leaf
+    // the points of leaf [s, e): a leaf after i's own that may hold neighbours
     auto test_leaf = [&](const unsigned lw, const int e) {
         const int s = (int)(lw & ~DENSE_BIT);
         if (STATS)
@@ -183,31 +272,46 @@ __device__ __forceinline__ void union_query(const int i, const float e2, const T
             }
         }
     };
-    const int me = my_leaf - (L - 1);
-    const int4 c4 = cand[me];
-    int resume = SENTINEL;
-    for (int c = 0; c < CAND_K; c++) {
-        const int v = c == 0 ? c4.x : c == 1 ? c4.y : c == 2 ? c4.z : c4.w;
-        if (v == SENTINEL)
-            break;
-        if (v < 0) {
-            resume = -v - 2;
-            break;
+    bool may_exit = SCHED == 2;
+    if (SCHED == 1) {
+        for (int c = 0; c < CAND_SLOTS; c++) {
+            const int v = c == 0 ? c4.y : c == 1 ? c4.z : c4.w;
+            if (v == SENTINEL)
+                break;
+            if (v < 0) {  // more candidates than the list holds: walk on from there
+                node = -v - 2;
+                // The early exit needs the highest split level crossed since
+                // i's leaf: that of the leaf boundaries between i's leaf and
+                // the resume leaf, which is the split level between the keys
+                // of the last point of the one and the first of the other
+                // (the highest differing bit of two sorted keys is the
+                // highest of those of the neighbouring pairs between them).
+                const int last_own = (own_end & ~(int)DENSE_BIT) - 1;
+                const int first = (int)(__float_as_uint(__ldg(T.nodes + 2 * (size_t)node).w) & ~DENSE_BIT);
+                M = split_level(sorted_key(T.st, T.k0, T.k1, last_own), sorted_key(T.st, T.k0, T.k1, first),
+                                last_own);
+                H = reach_level(p.x, p.y, p.z, p.x, p.y, p.z, g);
+                may_exit = true;
+                break;
+            }
+            // the leaf passed the leaf-box test; the point's own box test is
+            // tighter and spares the point tests of most far leaves
+            float4 lo, hi;
+            ld_node(T.nodes, L - 1 + v, lo, hi);
+            if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2)
+                test_leaf(__float_as_uint(lo.w), leaf_first[v + 1]);
         }
-        // the leaf passed the leaf-box test; the point's own box test is
-        // tighter and spares the point tests of most far leaves
-        const float4 lo = node_lo(T, L - 1 + v), hi = node_hi(T, L - 1 + v);
-        if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2)
-            test_leaf(__float_as_uint(lo.w), leaf_first[v + 1]);
     }
-    // more candidates than the list holds: the plain pair traversal from the
-    // leaf where the list ran out
-    int node = resume;
+    // the plain pair traversal: from i's own leaf (SCHED 2) or from the leaf
+    // where the candidate list ran out (SCHED 1, without the early exit: the
+    // levels crossed before that leaf are not known here)
     unsigned steps = 0;
     while (node != SENTINEL) {
         if (!node_ok(node, L, steps, dev_status))
             break;
-        const float4 lo = node_lo(T, node), hi = node_hi(T, node);
+        float4 lo, hi;
+        ld_node(T.nodes, node, lo, hi);
+        const int lv = level_of(hi);
         if (STATS)
             c_visit++;
         if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2) {
@@ -216,6 +320,11 @@ __device__ __forceinline__ void union_query(const int i, const float e2, const T
                 continue;
             }
             test_leaf(__float_as_uint(lo.w), leaf_first[node - (L - 1) + 1]);
+        }
+        if (may_exit) {
+            if (region_exit(lv, M, H))
+                break;
+            M = max(M, lv);
         }
         node = __float_as_int(hi.w);
     }
@@ -230,8 +339,9 @@ __device__ __forceinline__ void union_query(const int i, const float e2, const T
     }
 }
 
-template <bool FOF, bool STATS>
+template <int SCHED, bool FOF, bool STATS>
 __global__ void __launch_bounds__(1024, 2) k_union(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
+                        const unsigned long long *k0, const unsigned long long *k1,
                         const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
                         const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
                         const int4 *__restrict__ cand, int *parent,
@@ -243,17 +353,17 @@ __global__ void __launch_bounds__(1024, 2) k_union(int64_t n, const State *__res
     const int i = (int)i64;
     if (!FOF && !core[i])
         return;
-    const Tree T{nodes, leaf_first, st->n_leaves};
-    union_query<FOF, STATS>(i, seg[0].e2, T, spts, leaf_of, cand, parent, core, dev_status, stats);
+    const Tree T{nodes, leaf_first, st->n_leaves, st, k0, k1};
+    union_query<SCHED, FOF, STATS>(i, seg[0], T, spts, leaf_of, cand, parent, core, dev_status, stats);
 }
 
 // Many segments: each query takes its segment's eps and mode from its key.
-template <bool STATS>
+template <int SCHED, bool STATS>
 __global__ void __launch_bounds__(1024, 2) k_union_seg(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
                             const unsigned long long *k0, const unsigned long long *k1,
                             const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
                             const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
-                        const int4 *__restrict__ cand, int *parent,
+                            const int4 *__restrict__ cand, int *parent,
                             unsigned char *core, unsigned *dev_status, TravStats *stats)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,20 +371,41 @@ __global__ void __launch_bounds__(1024, 2) k_union_seg(int64_t n, const State *_
         return;
     const int i = (int)i64;
     const SegState &g = seg[seg_of_key(sorted_key(st, k0, k1, i), st->shift)];
-    const Tree T{nodes, leaf_first, st->n_leaves};
+    const Tree T{nodes, leaf_first, st->n_leaves, st, k0, k1};
     if (g.minpts <= 2)
-        union_query<true, STATS>(i, g.e2, T, spts, leaf_of, cand, parent, core, dev_status, stats);
+        union_query<SCHED, true, STATS>(i, g, T, spts, leaf_of, cand, parent, core, dev_status, stats);
     else if (core[i])
-        union_query<false, STATS>(i, g.e2, T, spts, leaf_of, cand, parent, core, dev_status, stats);
+        union_query<SCHED, false, STATS>(i, g, T, spts, leaf_of, cand, parent, core, dev_status, stats);
 }
 
 // ---- core counting with early termination (minPts > 2) -------------------------------
+
+// A walk from the root reaches the query's own leaf (the box of a leaf holds
+// its points); after it, the walk may stop at the first subtree it leaves that
+// holds the query's leaf and every cell a neighbour can have (region_exit).
+// M is the highest split level crossed since that leaf.
+struct RootWalkExit {
+    int own, H, M;
+    bool past;
+    __device__ __forceinline__ bool leave(int node, int lv)
+    {
+        if (node == own)
+            past = true;
+        if (!past)
+            return false;
+        if (region_exit(lv, M, H))
+            return true;
+        M = max(M, lv);
+        return false;
+    }
+};
 
 template <bool SEG>
 __global__ void k_count(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
                         const unsigned long long *k0, const unsigned long long *k1,
                         const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
-                        const int *__restrict__ leaf_first, unsigned char *core, unsigned *dev_status)
+                        const int *__restrict__ leaf_first, const int *__restrict__ leaf_of,
+                        unsigned char *core, unsigned *dev_status)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i64 >= n)
@@ -293,13 +424,16 @@ __global__ void k_count(int64_t n, const State *__restrict__ st, const SegState 
     const Tree T{nodes, leaf_first, st->n_leaves};
     const int L = T.L;
     const float4 p = spts[i];
+    RootWalkExit ex{L - 1 + leaf_of[i], reach_level(p.x, p.y, p.z, p.x, p.y, p.z, g), 0, false};
     int cnt = 0;
     int node = g.root;
     unsigned steps = 0;
     while (node != SENTINEL) {
         if (!node_ok(node, L, steps, dev_status))
             break;
-        const float4 lo = node_lo(T, node), hi = node_hi(T, node);
+        float4 lo, hi;
+        ld_node(nodes, node, lo, hi);
+        const int lv = level_of(hi);
         if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2) {
             if (node < L - 1) {
                 node = __float_as_int(lo.w);
@@ -315,6 +449,8 @@ __global__ void k_count(int64_t n, const State *__restrict__ st, const SegState 
                 }
             }
         }
+        if (ex.leave(node, lv))
+            break;
         node = __float_as_int(hi.w);
     }
 }
@@ -329,7 +465,8 @@ template <bool SEG>
 __global__ void k_border(int64_t n, const State *__restrict__ st, const SegState *__restrict__ seg,
                          const unsigned long long *k0, const unsigned long long *k1,
                          const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
-                         const int *__restrict__ leaf_first, int *parent, const unsigned char *__restrict__ core,
+                         const int *__restrict__ leaf_first, const int *__restrict__ leaf_of,
+                         int *parent, const unsigned char *__restrict__ core,
                          int *bmin, unsigned *dev_status)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -348,13 +485,16 @@ __global__ void k_border(int64_t n, const State *__restrict__ st, const SegState
     const Tree T{nodes, leaf_first, st->n_leaves};
     const int L = T.L;
     const float4 p = spts[i];
+    RootWalkExit ex{L - 1 + leaf_of[i], reach_level(p.x, p.y, p.z, p.x, p.y, p.z, g), 0, false};
     int best_k = 0x7fffffff, best_r = -1;
     int node = g.root;
     unsigned steps = 0;
     while (node != SENTINEL) {
         if (!node_ok(node, L, steps, dev_status))
             break;
-        const float4 lo = node_lo(T, node), hi = node_hi(T, node);
+        float4 lo, hi;
+        ld_node(nodes, node, lo, hi);
+        const int lv = level_of(hi);
         if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2) {
             if (node < L - 1) {
                 node = __float_as_int(lo.w);
@@ -379,6 +519,8 @@ __global__ void k_border(int64_t n, const State *__restrict__ st, const SegState
                 }
             }
         }
+        if (ex.leave(node, lv))
+            break;
         node = __float_as_int(hi.w);
     }
     if (best_r >= 0) {
@@ -428,74 +570,99 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t n, const State *__rest
         labels[o] = SEG ? lab - off[s] : lab;
 }
 
+template <int SCHED>
+static void launch_union(const Work &w, int g, int B, TravStats *stats, cudaStream_t s)
+{
+    if (w.nseg > 1) {
+        if (stats)
+            k_union_seg<SCHED, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
+                                                     w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
+                                                     w.dev_status, stats);
+        else
+            k_union_seg<SCHED, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
+                                                      w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
+                                                      w.dev_status, nullptr);
+    } else if (w.any_fof) {
+        if (stats)
+            k_union<SCHED, true, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
+                                                       w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
+                                                       w.dev_status, stats);
+        else
+            k_union<SCHED, true, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
+                                                        w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
+                                                        w.dev_status, nullptr);
+    } else {
+        if (stats)
+            k_union<SCHED, false, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
+                                                        w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
+                                                        w.dev_status, stats);
+        else
+            k_union<SCHED, false, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
+                                                         w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
+                                                         w.dev_status, nullptr);
+    }
+    note_launch();
+}
+
 void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t s)
 {
     const int B = p.block;
     const int g = div_up(w.n, B);
+    const bool seg = w.nseg > 1;
     TravStats *stats = (TravStats *)w.stats;
     cudaMemsetAsync(labels, 0xff, (size_t)w.n * sizeof(int32_t), s);  // noise = -1
-    if (w.nseg == 1)
-        k_cand<false><<<div_up(w.n, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.cand, w.dev_status);
-    else
-        k_cand<true><<<div_up(w.n, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.cand, w.dev_status);
-    note_launch();
+    if (p.schedule == 1) {
+        const int gc = (int)std::min<int64_t>(div_up(w.n, 256), (int64_t)g_cand_blocks_per_sm * w.n_sms);
+        if (seg)
+            k_cand<true><<<gc, 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.leaf_first, w.cand, w.dev_status);
+        else
+            k_cand<false><<<gc, 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.nodes, w.leaf_first, w.cand, w.dev_status);
+        note_launch();
+    }
     prof_mark(ST_CANDS, s);
-    if (w.nseg == 1) {
-        if (w.any_fof) {
-            if (stats)
-                k_union<true, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                    w.cand, w.parent, w.core, w.dev_status, stats);
-            else
-                k_union<true, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                     w.cand, w.parent, w.core, w.dev_status, nullptr);
-            note_launch();
-            prof_mark(ST_UNION, s);
-        } else {
+    if (w.any_dbscan) {
+        if (seg)
+            k_count<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
+                                          w.leaf_of, w.core, w.dev_status);
+        else
             k_count<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
-                                           w.core, w.dev_status);
-            note_launch();
-            prof_mark(ST_COUNT, s);
-            if (stats)
-                k_union<false, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                     w.cand, w.parent, w.core, w.dev_status, stats);
-            else
-                k_union<false, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.spts, w.nodes, w.leaf_of, w.leaf_first,
-                                                      w.cand, w.parent, w.core, w.dev_status, nullptr);
-            note_launch();
-            prof_mark(ST_UNION, s);
+                                           w.leaf_of, w.core, w.dev_status);
+        note_launch();
+        prof_mark(ST_COUNT, s);
+    }
+    if (p.schedule == 1)
+        launch_union<1>(w, g, B, stats, s);
+    else
+        launch_union<2>(w, g, B, stats, s);
+    prof_mark(ST_UNION, s);
+    if (w.any_dbscan) {
+        if (seg)
+            k_border<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
+                                           w.leaf_of, w.parent, w.core, w.bmin, w.dev_status);
+        else
             k_border<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
-                                            w.parent, w.core, w.bmin, w.dev_status);
-            note_launch();
-            prof_mark(ST_BORDER, s);
-        }
+                                            w.leaf_of, w.parent, w.core, w.bmin, w.dev_status);
+        note_launch();
+        prof_mark(ST_BORDER, s);
+    }
+    if (seg)
+        k_finalize<true><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.st, w.seg, w.seg_off, w.keys[0], w.keys[1], w.spts,
+                                                          w.parent, w.core, w.bmin, labels);
+    else
         k_finalize<false><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.st, w.seg, w.seg_off, w.keys[0], w.keys[1],
                                                            w.spts, w.parent, w.core, w.bmin, labels);
-    } else {
-        if (w.any_dbscan) {
-            k_count<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
-                                          w.core, w.dev_status);
-            note_launch();
-            prof_mark(ST_COUNT, s);
-        }
-        if (stats)
-            k_union_seg<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_of,
-                                              w.leaf_first, w.cand, w.parent, w.core, w.dev_status, stats);
-        else
-            k_union_seg<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_of,
-                                               w.leaf_first, w.cand, w.parent, w.core, w.dev_status, nullptr);
-        note_launch();
-        prof_mark(ST_UNION, s);
-        if (w.any_dbscan) {
-            k_border<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
-                                           w.parent, w.core, w.bmin, w.dev_status);
-            note_launch();
-            prof_mark(ST_BORDER, s);
-        }
-        k_finalize<true><<<div_up(w.n, 256), 256, 0, s>>>(w.n, w.st, w.seg, w.seg_off, w.keys[0], w.keys[1],
-                                                          w.spts, w.parent, w.core, w.bmin, labels);
-    }
     note_launch();
     prof_mark(ST_FINALIZE, s);
+}
+
+void cluster_init_device()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cand<true>, 256, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 4;
+    }
+    g_cand_blocks_per_sm = b;
 }
 
 }  // namespace abx

@@ -1,4 +1,4 @@
-// Scene bounds, Morton codes, onesweep LSD radix sort and the sorted gather.
+// Segments, scene bounds and the Morton quantisation step.
 //
 // Paper, subsection "64-bit Morton codes": points are ordered along a Z-curve
 // before the hierarchy is built; 64-bit codes avoid the massive duplication
@@ -16,11 +16,6 @@
 
 namespace abx {
 
-using u32 = unsigned;
-// Below this size the 32-bit key kernels are not launched (their launch costs
-// more than the lighter passes save).
-constexpr int64_t KEY32_MIN_POINTS = 1 << 16;
-
 // ---- segments and bounds -----------------------------------------------------------
 
 __device__ __forceinline__ void seg_reset(SegState &g, float eps, int minpts)
@@ -36,7 +31,7 @@ __device__ __forceinline__ void seg_reset(SegState &g, float eps, int minpts)
     g.bits = 0;
     g.dense_ok = 0;
     g.root = SENTINEL;
-    g.pad = 0;
+    g.margin = -1;
 }
 
 // A single clustering call: one segment covering all n points.
@@ -273,300 +268,24 @@ __global__ void k_quant(State *st, SegState *seg, const int *__restrict__ off, i
             inv_step = 0.0f;
         g.inv_step = inv_step;
         g.bits = bits;
+        // Cells two neighbours can be apart on one axis.  The test d2 <= e2 bounds
+        // each rounded square fl(d_a^2) <= d2 by e2, so |x - y| <= sqrt(e2) (1 + 2^-22)
+        // while e2 is a normal number and |x - y| < 2^-62 when it is not (eps_eff
+        // below).  In cells that is eps_eff * inv_step, plus the rounding of
+        // (x - lo) * inv_step wherever a cell is not clamped (under 2^(bits-22)
+        // cells; 2^(bits-20) is used), and the floor adds less than one cell, so
+        // the difference of two cells is at most the ceiling of the sum.
+        {
+            const double eps_eff = fmax(sqrt((double)g.e2), 0x1p-62) * (1.0 + 0x1p-20);
+            const double mc = ceil(eps_eff * (double)inv_step + ldexp(1.0, bits - 20));
+            g.margin = (isfinite(mc) && mc < (double)(1 << 22)) ? (int)mc : -1;
+        }
         g.dense_ok = dense_ok;
         atomicMax(&st->max_bits, bits);
         if (dense_ok)
             atomicOr(&st->dense_ok, 1);
         if (k == 0)
             st->bits = bits;
-    }
-}
-
-// ---- Morton keys + the upfront digit histograms ---------------------------------
-// key = segment << shift | Morton code (shift = 3 * the widest per-axis width),
-// so segments sort apart and each forms its own subtree.
-
-// Both key widths are launched; the one that does not match the call's key
-// width (decided here, on the device) returns at once.
-template <bool SEG, typename K>
-__global__ void __launch_bounds__(256) k_morton(const float *__restrict__ pts, int64_t n, State *st,
-                                                const SegState *__restrict__ seg, const int *__restrict__ off,
-                                                K *__restrict__ keys, unsigned *dev_status)
-{
-    const int nseg = st->nseg;
-    const int shift = 3 * st->max_bits;
-    const int kbits = st->seg_bits + shift;
-    const bool key32 = st->allow32 && kbits <= 32;
-    if (key32 != (sizeof(K) == 4))
-        return;
-    bool bad = false;
-    __shared__ unsigned sh[MAX_PASSES * RADIX];
-    for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x)
-        sh[i] = 0;
-    const int np = (kbits + RADIX_BITS - 1) / RADIX_BITS;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->shift = shift;
-        st->n_passes = np;
-        st->key32 = key32;
-    }
-    float lx = seg[0].lo[0], ly = seg[0].lo[1], lz = seg[0].lo[2], is = seg[0].inv_step;
-    float qmax = (float)((1u << seg[0].bits) - 1u);
-    __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long top = 0;
-        if (SEG) {
-            const int s = seg_of_input(off, nseg, i);
-            const SegState &g = seg[s];
-            lx = g.lo[0]; ly = g.lo[1]; lz = g.lo[2]; is = g.inv_step;
-            qmax = (float)((1u << g.bits) - 1u);
-            top = (unsigned long long)s << shift;
-        }
-        float x = __ldg(pts + 3 * i), y = __ldg(pts + 3 * i + 1), z = __ldg(pts + 3 * i + 2);
-        bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
-        float tx = (x - lx) * is, ty = (y - ly) * is, tz = (z - lz) * is;
-        unsigned qx = tx < qmax ? (unsigned)fmaxf(tx, 0.0f) : (unsigned)qmax;
-        unsigned qy = ty < qmax ? (unsigned)fmaxf(ty, 0.0f) : (unsigned)qmax;
-        unsigned qz = tz < qmax ? (unsigned)fmaxf(tz, 0.0f) : (unsigned)qmax;
-        unsigned long long key = top | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-        keys[i] = (K)key;
-        for (int p = 0; p < np; p++)
-            atomicAdd(&sh[p * RADIX + (unsigned)((key >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
-    }
-    if (bad)
-        atomicOr(dev_status, DEV_NONFINITE);
-    __syncthreads();
-    for (int i = threadIdx.x; i < np * RADIX; i += blockDim.x)
-        if (sh[i])
-            atomicAdd(&st->hist[0][0] + i, sh[i]);
-}
-
-// One block of RADIX threads: drop passes whose digit is the same for every
-// key (a stable pass over a constant digit changes nothing), turn histograms
-// into exclusive offsets and number the remaining passes.
-__global__ void k_sort_plan(State *st, int64_t n)
-{
-    __shared__ int active[MAX_PASSES];
-    const int d = threadIdx.x;
-    const int np = st->n_passes;
-    if (d < MAX_PASSES)
-        active[d] = d < np;
-    __syncthreads();
-    for (int p = 0; p < np; p++)
-        if ((int64_t)st->hist[p][d] == n)
-            active[p] = 0;
-    __syncthreads();
-    if (d < np) {
-        unsigned run = 0;
-        for (int k = 0; k < RADIX; k++) {
-            unsigned c = st->hist[d][k];
-            st->hist[d][k] = run;
-            run += c;
-        }
-    }
-    if (d == 0) {
-        int ord = 0;
-        for (int p = 0; p < MAX_PASSES; p++)
-            st->pass_ord[p] = active[p] ? ord++ : -1;
-        st->n_active = ord;
-    }
-}
-
-// ---- onesweep pass ------------------------------------------------------------------
-// One tile of sort_tile<K>() keys per block (tile ids handed out in launch order, so
-// a tile only ever waits on tiles that are already running).  Each warp ranks
-// its keys by digit with __match_any_sync, the tile publishes its digit counts,
-// looks back across earlier tiles for its global prefix (decoupled look-back,
-// bounded spins) and scatters through shared memory so that keys of one digit
-// leave as contiguous runs.
-
-constexpr unsigned long long LB_AGG = LB_FLAG_AGG;
-constexpr unsigned long long LB_PRE = LB_FLAG_PRE;
-
-constexpr int SORT_WARPS = SORT_THREADS / 32;
-static int g_sort_blocks_per_sm = SORT_MIN_BLOCKS;  // set per process by kernels_init_device
-template <typename K>
-constexpr size_t onesweep_smem()
-{
-    return sort_tile<K>() * (sizeof(K) + sizeof(unsigned)) + SORT_WARPS * RADIX * 4 + 2 * RADIX * 4;
-}
-
-template <typename K>
-__global__ void __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) k_onesweep(int pass, K *k0, K *k1, unsigned *v0, unsigned *v1,
-                                                              int64_t n, State *st, unsigned long long *lb_all,
-                                                              unsigned *dev_status)
-{
-    if (st->key32 != (sizeof(K) == 4))
-        return;
-    const int ord = st->pass_ord[pass];
-    if (ord < 0)
-        return;
-    const K *ksrc = (ord & 1) ? k1 : k0;
-    K *kdst = (ord & 1) ? k0 : k1;
-    const unsigned *vsrc = (ord & 1) ? v1 : v0;
-    unsigned *vdst = (ord & 1) ? v0 : v1;
-    const bool first = ord == 0;
-    const int shift = pass * RADIX_BITS;
-    constexpr int SORT_ITEMS = sort_items<K>();
-    constexpr int SORT_TILE = sort_tile<K>();
-    const int ntiles = div_up(n, SORT_TILE);
-    const unsigned nn = (unsigned)n;
-    unsigned long long *lb = lb_all + (size_t)pass * ntiles * RADIX;
-
-    extern __shared__ __align__(16) unsigned char smem[];
-    K *s_keys = reinterpret_cast<K *>(smem);
-    unsigned *s_vals = reinterpret_cast<unsigned *>(s_keys + SORT_TILE);
-    unsigned *s_whist = s_vals + SORT_TILE;      // [warps][RADIX]
-    unsigned *s_loc = s_whist + SORT_WARPS * RADIX;  // tile-local digit offsets
-    unsigned *s_glob = s_loc + RADIX;            // destination base per digit
-    __shared__ int s_tile;
-    __shared__ unsigned s_wsum[RADIX / 32];
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // persistent: each block takes tiles in ticket order until none are left
-    // (a tile only waits on tiles whose blocks are already working on them)
-    while (true) {
-        if (tid == 0)
-            s_tile = (int)atomicAdd(&st->tile_ctr[pass], 1u);
-        for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS)
-            s_whist[i] = 0;
-        __syncthreads();
-        const int tile = s_tile;
-        if (tile >= ntiles)
-            break;
-        // positions fit 32 bits: n < 2^31 and a tile ends at most SORT_TILE - 1 past n
-        const unsigned base = (unsigned)tile * SORT_TILE + (unsigned)warp * 32 * SORT_ITEMS + lane;
-
-        K key[SORT_ITEMS];
-        unsigned val[SORT_ITEMS];
-        unsigned rank[SORT_ITEMS];
-    #pragma unroll
-        for (int k = 0; k < SORT_ITEMS; k++) {
-            const unsigned pos = base + k * 32;
-            key[k] = pos < nn ? ksrc[pos] : (K)~(K)0;  // pads rank last in digit RADIX-1 and land at >= n
-        }
-    #pragma unroll
-        for (int k = 0; k < SORT_ITEMS; k++) {
-            const unsigned pos = base + k * 32;
-            val[k] = pos < nn ? (first ? pos : vsrc[pos]) : 0u;
-        }
-        // stable rank within the warp: lanes with equal digit, in lane order, after
-        // the earlier items of this warp.  The lanes sharing a digit are found
-        // with one ballot per digit bit (cheaper than a general match).
-        unsigned *wh = s_whist + warp * RADIX;
-        const unsigned lt_mask = (1u << lane) - 1u;
-    #pragma unroll
-        for (int k = 0; k < SORT_ITEMS; k++) {
-            const unsigned d = (unsigned)(key[k] >> shift) & (RADIX - 1);
-            unsigned peers = ~0u;
-    #pragma unroll
-            for (int b = 0; b < RADIX_BITS; b++) {
-                const bool bit = (d >> b) & 1u;
-                const unsigned bal = __ballot_sync(~0u, bit);
-                peers &= bit ? bal : ~bal;
-            }
-            const int leader = __ffs(peers) - 1;
-            unsigned prev = 0;
-            if (lane == leader)
-                prev = atomicAdd(wh + d, (unsigned)__popc(peers));
-            prev = __shfl_sync(~0u, prev, leader);
-            rank[k] = prev + __popc(peers & lt_mask);
-        }
-        __syncthreads();
-
-        // thread d < RADIX: per-warp exclusive offsets and the tile count of digit d
-        unsigned cnt = 0;
-        unsigned long long excl = 0;
-        if (tid < RADIX) {
-            const int d = tid;
-    #pragma unroll
-            for (int w = 0; w < SORT_WARPS; w++) {
-                unsigned c = s_whist[w * RADIX + d];
-                s_whist[w * RADIX + d] = cnt;
-                cnt += c;
-            }
-            // publish, then look back
-            if (tile == 0) {
-                lb_store(lb + d, LB_PRE | cnt);
-            } else {
-                lb_store(lb + (size_t)tile * RADIX + d, LB_AGG | cnt);
-                excl = lookback<8>(lb, tile, RADIX, tid, dev_status);
-                lb_store(lb + (size_t)tile * RADIX + d, LB_PRE | (excl + cnt));
-            }
-        }
-        // exclusive scan of cnt over digits (tile-local offsets)
-        unsigned x = cnt;
-    #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(~0u, x, o);
-            if (lane >= o)
-                x += y;
-        }
-        if (tid < RADIX && lane == 31)
-            s_wsum[warp] = x;
-        __syncthreads();
-        if (tid < RADIX) {
-            unsigned wpre = 0;
-            for (int w = 0; w < warp; w++)
-                wpre += s_wsum[w];
-            const unsigned loc = wpre + x - cnt;
-            s_loc[tid] = loc;
-            s_glob[tid] = st->hist[pass][tid] + (unsigned)excl - loc;
-        }
-        __syncthreads();
-
-    #pragma unroll
-        for (int k = 0; k < SORT_ITEMS; k++) {
-            const unsigned dd = (unsigned)(key[k] >> shift) & (RADIX - 1);
-            const unsigned lp = s_loc[dd] + s_whist[warp * RADIX + dd] + rank[k];
-            s_keys[lp] = key[k];
-            s_vals[lp] = val[k];
-        }
-        __syncthreads();
-    #pragma unroll 4
-        for (int i = tid; i < SORT_TILE; i += SORT_THREADS) {
-            const K kk = s_keys[i];
-            const unsigned dd = (unsigned)(kk >> shift) & (RADIX - 1);
-            const unsigned dest = s_glob[dd] + (unsigned)i;
-            if (dest < nn) {
-                kdst[dest] = kk;
-                vdst[dest] = s_vals[i];
-            }
-        }
-        __syncthreads();  // the next tile reuses the shared buffers
-    }
-}
-
-// ---- gather -----------------------------------------------------------------------
-// spts[k] = (x, y, z, original index) of the k-th point in key order; resets
-// the union-find, the core flags (all core when the segment's minPts is 1)
-// and the border minima.
-
-template <bool SEG>
-__global__ void __launch_bounds__(256) k_gather(const float *__restrict__ pts, int64_t n, const State *st,
-                                                const SegState *__restrict__ seg, const void *k0,
-                                                const void *k1, const unsigned *v0, const unsigned *v1,
-                                                float4 *spts, int *parent, unsigned char *core, int *bmin,
-                                                unsigned *dev_status)
-{
-    const int na = st->n_active;
-    const unsigned *perm = na == 0 ? nullptr : ((na & 1) ? v1 : v0);
-    const int shift = st->shift;
-    unsigned char c0 = seg[0].minpts <= 1 ? 1 : 0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        unsigned o = perm ? perm[k] : (unsigned)k;
-        if ((int64_t)o >= n) {  // never for a correct sort
-            atomicOr(dev_status, DEV_INTERNAL);
-            o = (unsigned)k;
-        }
-        float x = __ldg(pts + 3 * (int64_t)o), y = __ldg(pts + 3 * (int64_t)o + 1), z = __ldg(pts + 3 * (int64_t)o + 2);
-        spts[k] = make_float4(x, y, z, __int_as_float((int)o));
-        parent[k] = (int)k;
-        if (SEG)
-            c0 = seg[seg_of_key(sorted_key(st, k0, k1, k), shift)].minpts <= 1 ? 1 : 0;
-        core[k] = c0;
-        if (bmin)
-            bmin[k] = 0x7fffffff;
     }
 }
 
@@ -612,75 +331,6 @@ void stage_bounds_quant(const Work &w, const float *points, const Params &p, cud
     k_quant<<<div_up(w.nseg, 128), 128, 0, s>>>(w.st, w.seg, w.seg_off, w.nseg, p.dense, p.sub_bits);
     note_launch(2);
     prof_mark(ST_BOUNDS, s);
-}
-
-void stage_morton_sort(const Work &w, const float *points, cudaStream_t s)
-{
-    using u64 = unsigned long long;
-    u32 *k32[2] = {reinterpret_cast<u32 *>(w.keys[0]), reinterpret_cast<u32 *>(w.keys[1])};
-    const bool try32 = w.n >= KEY32_MIN_POINTS;  // must match the allow32 given to the init kernel
-    const int g = grid_for(w, w.n, 256);
-    if (w.nseg == 1) {
-        k_morton<false, u64><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0], w.dev_status);
-        if (try32)
-            k_morton<false, u32><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, k32[0], w.dev_status);
-    } else {
-        k_morton<true, u64><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0], w.dev_status);
-        if (try32)
-            k_morton<true, u32><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, k32[0], w.dev_status);
-    }
-    note_launch(try32 ? 2 : 1);
-    prof_mark(ST_MORTON, s);
-    k_sort_plan<<<1, RADIX, 0, s>>>(w.st, w.n);
-    note_launch();
-    cudaMemsetAsync(w.sort_lb, 0, (size_t)MAX_PASSES * w.sort_tiles * RADIX * sizeof(unsigned long long), s);
-    const int tiles = (int)std::min<int64_t>(div_up(w.n, SORT_TILE_MIN), (int64_t)g_sort_blocks_per_sm * w.n_sms);
-    for (int pass = 0; pass < MAX_PASSES; pass++)
-        k_onesweep<u64><<<tiles, SORT_THREADS, onesweep_smem<u64>(), s>>>(pass, w.keys[0], w.keys[1], w.vals[0],
-                                                                          w.vals[1], w.n, w.st, w.sort_lb,
-                                                                          w.dev_status);
-    note_launch(MAX_PASSES);
-    if (try32) {
-        for (int pass = 0; pass < 4; pass++)
-            k_onesweep<u32><<<tiles, SORT_THREADS, onesweep_smem<u32>(), s>>>(pass, k32[0], k32[1], w.vals[0],
-                                                                              w.vals[1], w.n, w.st, w.sort_lb,
-                                                                              w.dev_status);
-        note_launch(4);
-    }
-    prof_mark(ST_SORT, s);
-}
-
-void stage_gather(const Work &w, const float *points, cudaStream_t s)
-{
-    int *bmin = w.any_dbscan ? w.bmin : nullptr;
-    if (w.nseg == 1)
-        k_gather<false><<<grid_for(w, w.n, 256, 16), 256, 0, s>>>(points, w.n, w.st, w.seg, w.keys[0], w.keys[1],
-                                                                  w.vals[0], w.vals[1], w.spts, w.parent, w.core,
-                                                                  bmin, w.dev_status);
-    else
-        k_gather<true><<<grid_for(w, w.n, 256, 16), 256, 0, s>>>(points, w.n, w.st, w.seg, w.keys[0], w.keys[1],
-                                                                 w.vals[0], w.vals[1], w.spts, w.parent, w.core,
-                                                                 bmin, w.dev_status);
-    note_launch();
-    prof_mark(ST_GATHER, s);
-}
-
-void kernels_init_device()
-{
-    int b32 = 0, b64 = 0;
-    cudaFuncSetAttribute(k_onesweep<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)onesweep_smem<unsigned long long>());
-    cudaFuncSetAttribute(k_onesweep<u32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<u32>());
-    // persistent sort grid: as many blocks as fit on an SM (both key widths
-    // share one grid size)
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_onesweep<unsigned long long>, SORT_THREADS,
-                                                      onesweep_smem<unsigned long long>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_onesweep<u32>, SORT_THREADS,
-                                                      onesweep_smem<u32>()) != cudaSuccess) {
-        cudaGetLastError();
-        b32 = b64 = SORT_MIN_BLOCKS;
-    }
-    g_sort_blocks_per_sm = std::max(1, std::min(b32, b64));
 }
 
 }  // namespace abx

@@ -220,21 +220,6 @@ __global__ void __launch_bounds__(256) k_dense_cells(int64_t n, State *st, const
 // Record i (two float4): internal node i < L-1: (lo, left child), (hi, rope);
 // leaf t at i = L-1+t: (lo, first point | DENSE_BIT), (hi, rope).
 
-__device__ __forceinline__ unsigned char split_level(unsigned long long a, unsigned long long b, int t)
-{
-    unsigned long long x = a ^ b;
-    if (x)
-        return (unsigned char)(32 + (64 - __clzll((long long)x)));
-    return (unsigned char)(32 - __clz(t ^ (t + 1)));
-}
-
-__global__ void __launch_bounds__(256) k_pdelta(int64_t n, const State *st, const unsigned long long *k0,
-                                                const unsigned long long *k1, unsigned char *pdelta)
-{
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n - 1; k += (int64_t)gridDim.x * blockDim.x)
-        pdelta[k] = split_level(sorted_key(st, k0, k1, k), sorted_key(st, k0, k1, k + 1), (int)k);
-}
-
 __global__ void __launch_bounds__(256) k_leaves(const State *st, SegState *seg, const unsigned long long *k0,
                                                 const unsigned long long *k1, const unsigned char *__restrict__ pdelta,
                                                 const float4 *__restrict__ spts, const int *leaf_first,
@@ -451,21 +436,31 @@ __global__ void __launch_bounds__(256) k_build_global(State *st, SegState *seg, 
     }
 }
 
-// rope(node covering [.., b]) = right child of internal node b, or the sentinel
+// rope(node covering [.., b]) = right child of internal node b, or the
+// sentinel; the split level of leaf boundary b, which following the rope
+// crosses (255 with the sentinel), goes into the low bits of hi.x for the
+// early exit of the rope walks (with_level).
 __global__ void __launch_bounds__(256) k_ropes(const State *st, float4 *nodes, const int *right_of,
-                                               const int *leaf_seg, unsigned *dev_status)
+                                               const int *leaf_seg, const unsigned char *__restrict__ delta,
+                                               unsigned *dev_status)
 {
     const int L = st->n_leaves;
     const int nseg = st->nseg;
     const int total = 2 * L - 1;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        int b = i < L - 1 ? __float_as_int(nodes[2 * (size_t)i + 1].w) : i - (L - 1);
+        float4 hi = nodes[2 * (size_t)i + 1];
+        const int b = i < L - 1 ? __float_as_int(hi.w) : i - (L - 1);
         int rope = SENTINEL;
-        if ((unsigned)b >= (unsigned)L)
+        unsigned lv = 255;
+        if ((unsigned)b >= (unsigned)L) {
             atomicOr(dev_status, DEV_INTERNAL);  // node never completed: corrupted build
-        else if (b != L - 1 && (nseg == 1 || leaf_seg[b] == leaf_seg[b + 1]))
+        } else if (b != L - 1 && (nseg == 1 || leaf_seg[b] == leaf_seg[b + 1])) {
             rope = right_of[b];  // else: last leaf of its segment -> sentinel
-        reinterpret_cast<int *>(nodes + 2 * (size_t)i + 1)[3] = rope;
+            lv = delta[b];
+        }
+        hi.x = with_level(hi.x, lv);
+        hi.w = __int_as_float(rope);
+        nodes[2 * (size_t)i + 1] = hi;
     }
 }
 
@@ -488,7 +483,6 @@ void stage_cells_leaves(const Work &w, const Params &p, cudaStream_t s)
                                                             w.dense_root, p.dense_min);
     note_launch(1);
     prof_mark(ST_CELLS, s);
-    k_pdelta<<<grid_cap(w, w.n, 256, 16), 256, 0, s>>>(w.n, w.st, w.keys[0], w.keys[1], w.pdelta);
     cudaMemsetAsync(w.scan_lb, 0, w.scan_tiles * sizeof(unsigned long long), s);
     LeafFlag lf{w.dense_root, w.pdelta, w.parent, w.core, w.st, w.keys[0], w.keys[1], p.leaf_size, w.n};
     k_flag_scan<<<scan_tiles, SCAN_THREADS, 0, s>>>(w.n, lf, w.leaf_of, w.leaf_first, &w.st->n_leaves,
@@ -496,7 +490,7 @@ void stage_cells_leaves(const Work &w, const Params &p, cudaStream_t s)
                                                     0);
     k_leaves<<<grid_cap(w, w.n, 256), 256, 0, s>>>(w.st, w.seg, w.keys[0], w.keys[1], w.pdelta, w.spts, w.leaf_first,
                                                    w.dense_root, w.nodes, w.delta, w.leaf_seg);
-    note_launch(3);
+    note_launch(2);
     prof_mark(ST_LEAVES, s);
 }
 
@@ -508,7 +502,8 @@ void stage_hierarchy(const Work &w, cudaStream_t s)
                                                                             &w.st->frontier_count);
     k_build_global<<<grid_cap(w, w.n / 16 + 1, 256), 256, 0, s>>>(w.st, w.seg, w.leaf_seg, w.delta, w.nodes, w.slot,
                                                                   w.right_of, w.frontier, &w.st->frontier_count);
-    k_ropes<<<grid_cap(w, 2 * w.n, 256), 256, 0, s>>>(w.st, w.nodes, w.right_of, w.leaf_seg, w.dev_status);
+    k_ropes<<<grid_cap(w, 2 * w.n, 256), 256, 0, s>>>(w.st, w.nodes, w.right_of, w.leaf_seg, w.delta,
+                                                      w.dev_status);
     note_launch(3);
     prof_mark(ST_BUILD, s);
 }

@@ -1,0 +1,75 @@
+// Morton keys of the input points, shared by the histogram pass and the
+// bucketing pass (which recomputes them instead of reading them back).
+//
+// key = segment << shift | Morton code (shift = 3 * the widest per-axis width),
+// so segments sort apart and each forms its own subtree.  Each axis is
+// quantised with its segment's step (quant_axis: the same rounded expression
+// the early exit of the rope walks relies on) and the three cell indices are
+// interleaved, x in bit 3k + 2, y in 3k + 1, z in 3k (paper, subsection
+// "64-bit Morton codes").
+#pragma once
+
+#include "work.cuh"
+
+namespace abx {
+
+template <bool SEG>
+struct KeyGen {
+    const float *pts;
+    const SegState *seg;
+    const int *off;
+    int nseg, shift;
+    float lx, ly, lz, is, qmax;  // segment 0's grid (the single-segment case)
+
+    __device__ KeyGen(const float *p, const State *st, const SegState *sg, const int *o)
+        : pts(p), seg(sg), off(o), nseg(st->nseg), shift(3 * st->max_bits)
+    {
+        lx = sg[0].lo[0];
+        ly = sg[0].lo[1];
+        lz = sg[0].lo[2];
+        is = sg[0].inv_step;
+        qmax = (float)((1u << sg[0].bits) - 1u);
+    }
+
+    // Key of input point i; `bad` is set if a coordinate is not finite.
+    __device__ __forceinline__ unsigned long long key(int64_t i, bool &bad) const
+    {
+        float4 p;
+        return key(i, bad, p);
+    }
+
+    // The same, also handing back the point as (x, y, z, i).
+    __device__ __forceinline__ unsigned long long key(int64_t i, bool &bad, float4 &pt) const
+    {
+        float x0 = lx, y0 = ly, z0 = lz, s = is, qm = qmax;
+        unsigned long long top = 0;
+        if (SEG) {
+            const int sg = seg_of_input(off, nseg, i);
+            const SegState &g = seg[sg];
+            x0 = g.lo[0];
+            y0 = g.lo[1];
+            z0 = g.lo[2];
+            s = g.inv_step;
+            qm = (float)((1u << g.bits) - 1u);
+            top = (unsigned long long)sg << shift;
+        }
+        const float x = __ldg(pts + 3 * i), y = __ldg(pts + 3 * i + 1), z = __ldg(pts + 3 * i + 2);
+        pt = make_float4(x, y, z, __int_as_float((int)i));
+        bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
+        const unsigned qx = quant_axis(x, x0, s, qm);
+        const unsigned qy = quant_axis(y, y0, s, qm);
+        const unsigned qz = quant_axis(z, z0, s, qm);
+        return top | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    }
+};
+
+// Width of the key in bits, and the shift that leaves its top RADIX_BITS
+// bits: the bucket digit.
+__device__ __forceinline__ int key_bits(const State *st) { return st->seg_bits + 3 * st->max_bits; }
+__device__ __forceinline__ int bucket_shift(const State *st)
+{
+    const int kb = key_bits(st);
+    return kb > RADIX_BITS ? kb - RADIX_BITS : 0;
+}
+
+}  // namespace abx

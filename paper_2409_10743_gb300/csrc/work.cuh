@@ -12,6 +12,8 @@ struct Params {
     int sub_bits;    // Morton bits per axis below the dense-cell side
     int block;       // threads per block of the traversal kernels
     int dense_min;   // a dense cell needs at least max(minPts, 2, dense_min) points
+    int schedule;    // pair traversal: 1 = candidate lists per leaf, then per point; 2 = per point
+    int digit_bits;  // radix-sort digit width (8, 10 or 11)
 };
 
 // Device buffers of one call; sizes are for n points (L <= n leaves).
@@ -22,7 +24,9 @@ struct Work {
     State *st;
     unsigned long long *keys[2];     // Morton keys, radix double buffer
     unsigned *vals[2];               // original indices, radix double buffer
-    unsigned long long *sort_lb;     // [MAX_PASSES][tiles][RADIX] look-back words
+    unsigned long long *sort_lb;     // [MAX_PASSES + 1][tiles][RADIX] look-back words (last row: buckets)
+    float4 *bpts;                    // [n] points in bucket order (x, y, z, original index); aliases
+                                     // nodes, which are written only after the gather has read it
     unsigned long long *scan_lb;     // [scan tiles] look-back words
     float4 *spts;                    // sorted points: x, y, z, original index (as int bits)
     int *dense_root;                 // [n] root of the point's dense cell, or -1
@@ -75,10 +79,15 @@ void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t
 // Parameter resolution (0 fields = defaults) and the autotuner's table.
 abx_status resolve_params(const abx_params *in, Params &p);
 bool tune_lookup(int64_t n, int32_t minpts, abx_params *out);
+bool tune_lookup_batch(int64_t n, bool any_dbscan, abx_params *out);
+
+// The no-allocation entry point's device status word, read and cleared.
+abx_status noalloc_take_status(unsigned *out);
 
 // One-time per-device kernel attributes.
 void kernels_init_device();
 void tree_init_device();
+void cluster_init_device();
 
 // Stage timers and launch accounting (profile mode records a CUDA event on the
 // launching stream at each stage boundary).

@@ -69,6 +69,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.abx_dbscan_ex(fake, 10, 0.1, 2, fake, ctypes.byref(bad), null) == ABX_EINVAL
     bad = Params(dense_cells=2)
     assert lib.abx_dbscan_ex(fake, 10, 0.1, 2, fake, ctypes.byref(bad), null) == ABX_EINVAL
+    for bad in (Params(schedule=3), Params(schedule=-1), Params(sort_digit_bits=9), Params(sort_digit_bits=12)):
+        assert lib.abx_dbscan_ex(fake, 10, 0.1, 2, fake, ctypes.byref(bad), null) == ABX_EINVAL
 
 
 def test_graph_arguments_rejected_on_host(lib):
@@ -107,9 +109,12 @@ def test_bvh_arguments_rejected_on_host(lib):
     null = ctypes.c_void_p(0)
     fake = ctypes.c_void_p(0x1000)
     h = ctypes.c_void_p()
-    assert lib.abx_bvh_build(fake, 0, 0, ctypes.byref(h), null) == ABX_EINVAL
-    assert lib.abx_bvh_build(fake, 10, 64, ctypes.byref(h), null) == ABX_EINVAL
-    assert lib.abx_bvh_build(null, 10, 0, ctypes.byref(h), null) == ABX_EINVAL
+    from paper_2409_10743_gb300.binding import Params
+    assert lib.abx_bvh_build(fake, 0, None, ctypes.byref(h), null) == ABX_EINVAL
+    assert lib.abx_bvh_build(fake, 10, ctypes.byref(Params(leaf_size=64)), ctypes.byref(h), null) == ABX_EINVAL
+    assert lib.abx_bvh_build(fake, 10, ctypes.byref(Params(schedule=3)), ctypes.byref(h), null) == ABX_EINVAL
+    assert lib.abx_bvh_build(fake, 10, ctypes.byref(Params(sort_digit_bits=9)), ctypes.byref(h), null) == ABX_EINVAL
+    assert lib.abx_bvh_build(null, 10, None, ctypes.byref(h), null) == ABX_EINVAL
     assert lib.abx_bvh_count(null, fake, 1, 0.1, 1, fake, null) == ABX_EINVAL
     assert lib.abx_bvh_first_hit(null, fake, 1, 0.1, fake, null) == ABX_EINVAL
     assert lib.abx_bvh_destroy(null) == ABX_EINVAL

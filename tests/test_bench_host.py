@@ -24,7 +24,7 @@ def test_stage_bytes_table():
     assert bench.stage_bytes("sort", c32, n) == pytest.approx(12 + 3 * 16)
     assert bench.stage_bytes("sort", c64, n) == pytest.approx(20 + 3 * 24)
     assert bench.stage_bytes("morton", c32, n) == 16 and bench.stage_bytes("morton", c64, n) == 20
-    assert bench.stage_bytes("gather", c32, n) == 37
+    assert bench.stage_bytes("gather", c32, n) == 32  # perm 4 + point 12 + sorted float4 16
     assert bench.stage_bytes("union", c32, n) == pytest.approx(25 + 64 * per_leaf)
     assert bench.stage_bytes("candidates", c32, n) == pytest.approx(48 * per_leaf)
     assert bench.stage_bytes("no-such-stage", c32, n) == 0

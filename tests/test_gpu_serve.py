@@ -137,3 +137,29 @@ def test_invalid_tickets_and_arguments(abx):
         assert srv.wait(t, 1000)[0] == abx.ABX_OK
     finally:
         srv.close()
+
+
+def test_device_request_waits_for_its_producer_stream(abx):
+    """Device points written by work still queued on another stream at submit
+    time: the server must read them only after that work (the producer stream
+    passed to submit), not whatever the buffer held before."""
+    from workloads import clumps
+    p = clumps(60_000, 40, 4711, a0=0.01)
+    eps, minpts = 0.004, 3
+    want = oracle.dbscan(p, eps, minpts)
+    src = torch.from_numpy(p).cuda()
+    dst = torch.zeros_like(src)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    srv = abx.Server(max_slots=2)
+    try:
+        with torch.cuda.stream(side):
+            torch.cuda._sleep(100_000_000)  # a bounded spin (~50 ms) ahead of the copy
+            dst.copy_(src)
+        t = srv.submit(dst, eps, minpts, stream=side)
+        st, lab = srv.wait(t, 60_000)
+        assert st == 0, abx.status_str(st)
+        assert np.array_equal(lab.cpu().numpy(), want)
+    finally:
+        srv.close()
+        side.synchronize()
