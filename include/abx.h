@@ -86,8 +86,8 @@ typedef struct CUstream_st *abx_stream;
  *                leaf's box collecting candidate leaves, then one thread per
  *                point testing them (the default); 2 = one pass, every point
  *                walks the ropes from its own leaf with its own box
- *   sort_digit_bits  bits per radix-sort digit (8, 10 or 11; default 8): wider
- *                digits take fewer passes over the keys
+ *   sort_digit_bits  bits per radix-sort digit: 8 (the default, and the only
+ *                width built; any other value returns ABX_EINVAL)
  */
 typedef struct abx_params {
     int32_t leaf_size;
@@ -349,9 +349,12 @@ typedef struct abx_serve_report {
 
 typedef struct abx_server abx_server;
 
-/* Create a server (cfg may be NULL for defaults).  Host-side fault injection
- * for tests: ABX_SERVE_FAULT=hold admits nothing, =alloc fails every batch's
- * device allocation (read at creation). */
+/* Create a server (cfg may be NULL for defaults).  Host-resident requests are
+ * read and written by copy kernels on the slot's stream where the GPU can
+ * address pageable host memory (cudaDevAttrPageableMemoryAccess), else staged
+ * through pinned buffers; ABX_SERVE_STAGING=1 forces the staging.  Host-side
+ * fault injection for tests: ABX_SERVE_FAULT=hold admits nothing, =alloc
+ * fails every batch's device allocation.  (Both read at creation.) */
 abx_status abx_serve_create(const abx_serve_config *cfg, abx_server **out);
 
 /*

@@ -153,7 +153,8 @@ static void carve(Carver &c, Work &w, int64_t n, int nseg)
     w.keys[1] = c.take<unsigned long long>(N);
     w.vals[0] = c.take<unsigned>(N);
     w.vals[1] = c.take<unsigned>(N);
-    w.sort_lb = c.take<unsigned long long>((size_t)(MAX_PASSES + 1) * w.sort_tiles * RADIX);
+    w.bucket_tiles = (size_t)div_up(n, BUCKET_TILE);
+    w.sort_lb = c.take<unsigned long long>(((size_t)MAX_PASSES * w.sort_tiles + w.bucket_tiles) * RADIX);
     w.scan_lb = c.take<unsigned long long>(w.scan_tiles);
     w.spts = c.take<float4>(N);
     w.dense_root = c.take<int>(N);
@@ -206,7 +207,7 @@ abx_status resolve_params(const abx_params *in, Params &p)
         p.schedule = in->schedule;
     }
     if (in->sort_digit_bits) {
-        if (in->sort_digit_bits != 8 && in->sort_digit_bits != 10 && in->sort_digit_bits != 11)
+        if (in->sort_digit_bits != RADIX_BITS)
             return ABX_EINVAL;
         p.digit_bits = in->sort_digit_bits;
     }
@@ -308,8 +309,19 @@ static abx_status check_args(const float *points, int64_t n, float eps, int32_t 
     return ABX_OK;
 }
 
+// One clustering; the workspace (work_bytes(n)) is `ws_given` when the caller
+// carved it out of a larger block, else it is taken from the pool here.
+static abx_status dbscan_run(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
+                             const abx_params *params, abx_stream stream, void *ws_given);
+
 abx_status abx_dbscan_ex(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
                          const abx_params *params, abx_stream stream)
+{
+    return dbscan_run(points, n, eps, minpts, labels, params, stream, nullptr);
+}
+
+static abx_status dbscan_run(const float *points, int64_t n, float eps, int32_t minpts, int32_t *labels,
+                             const abx_params *params, abx_stream stream, void *ws_given)
 {
     abx_status rc = check_args(points, n, eps, minpts, labels);
     if (rc != ABX_OK)
@@ -326,8 +338,8 @@ abx_status abx_dbscan_ex(const float *points, int64_t n, float eps, int32_t minp
     if ((rc = device_ctx(&ctx)) != ABX_OK)
         return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    void *ws = nullptr;
-    if (cudaMallocFromPoolAsync(&ws, work_bytes(n), ctx->pool, s) != cudaSuccess) {
+    void *ws = ws_given;
+    if (!ws && cudaMallocFromPoolAsync(&ws, work_bytes(n), ctx->pool, s) != cudaSuccess) {
         cudaGetLastError();
         return ABX_ENOMEM;
     }
@@ -354,7 +366,8 @@ abx_status abx_dbscan_ex(const float *points, int64_t n, float eps, int32_t minp
     if (w.stats)
         cudaMemcpyAsync(g_stats_host, g_stats_dev, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(ws, s);
+    if (!ws_given)
+        cudaFreeAsync(ws, s);
     return cuda_status(e);
 }
 
@@ -496,21 +509,21 @@ abx_status abx_dbscan_host(const float *points_host, int64_t n, float eps, int32
     if ((rc = device_ctx(&ctx)) != ABX_OK)
         return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    void *dp = nullptr, *dl = nullptr;
-    if (cudaMallocFromPoolAsync(&dp, (size_t)n * 3 * sizeof(float), ctx->pool, s) != cudaSuccess ||
-        cudaMallocFromPoolAsync(&dl, (size_t)n * sizeof(int32_t), ctx->pool, s) != cudaSuccess) {
+    // one block of the same size on every call (points, labels, workspace):
+    // the pool hands the same memory back instead of growing
+    const size_t b_pts = align256((size_t)n * 3 * sizeof(float)), b_lab = align256((size_t)n * sizeof(int32_t));
+    char *blk = nullptr;
+    if (cudaMallocFromPoolAsync((void **)&blk, b_pts + b_lab + work_bytes(n), ctx->pool, s) != cudaSuccess) {
         cudaGetLastError();
-        if (dp)
-            cudaFreeAsync(dp, s);
-        cudaStreamSynchronize(s);
         return ABX_ENOMEM;
     }
+    float *dp = reinterpret_cast<float *>(blk);
+    int32_t *dl = reinterpret_cast<int32_t *>(blk + b_pts);
     cudaMemcpyAsync(dp, points_host, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
-    rc = abx_dbscan_ex(static_cast<const float *>(dp), n, eps, minpts, static_cast<int32_t *>(dl), nullptr, stream);
+    rc = dbscan_run(dp, n, eps, minpts, dl, nullptr, stream, blk + b_pts + b_lab);
     if (rc == ABX_OK)
         cudaMemcpyAsync(labels_host, dl, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(dp, s);
-    cudaFreeAsync(dl, s);
+    cudaFreeAsync(blk, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (rc != ABX_OK)
         return rc;

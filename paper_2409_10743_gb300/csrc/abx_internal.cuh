@@ -38,7 +38,9 @@ constexpr int64_t KEY32_MIN_POINTS = 1 << 16;
 // that reads the input in order); the gather after the sort then reads
 // within one or two buckets at a time, which L2 holds.
 constexpr int64_t BUCKET_MIN_POINTS = 1 << 23;
-constexpr int BUCKET_ROW = MAX_PASSES;          // its histogram row and look-back row
+constexpr int BUCKET_ITEMS = 8;                 // keys per thread of its tiles
+constexpr int BUCKET_TILE = SORT_THREADS * BUCKET_ITEMS;
+constexpr int BUCKET_ROW = MAX_PASSES;          // its histogram row; its look-back words follow the passes'
 constexpr int BUCKET_TICKETS = MAX_PASSES + 2;  // its tile counter (tile_ctr index)
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;

@@ -86,6 +86,8 @@ struct abx_server {
     size_t bytes_in_use = 0, peak_bytes = 0;
     bool stop = false;
     bool fault_hold = false, fault_alloc = false;
+    bool direct_host = false;  // kernels may read and write pageable host memory
+                               // (cudaDevAttrPageableMemoryAccess): no staging copies
     // statistics
     uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, batches = 0, batched_requests = 0;
     std::vector<double> latencies;
@@ -93,6 +95,26 @@ struct abx_server {
 };
 
 namespace {
+
+// Where the GPU can address pageable host memory (systems whose GPU shares
+// the host's page tables), a host request's points are read and its labels
+// written by these copies on the slot's stream, asynchronous like the rest of
+// the batch; elsewhere they go through pinned staging buffers.
+__global__ void __launch_bounds__(256) k_copy_words(unsigned *__restrict__ dst, const unsigned *__restrict__ src,
+                                                    int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+void copy_words(void *dst, const void *src, int64_t words, cudaStream_t s)
+{
+    if (words <= 0)
+        return;
+    const int64_t g = std::min<int64_t>((words + 255) / 256, 152 * 16);
+    k_copy_words<<<(int)g, 256, 0, s>>>(static_cast<unsigned *>(dst), static_cast<const unsigned *>(src), words);
+    note_launch();
+}
 
 // Host copies of large staging buffers are split over a few threads (one core
 // copies pageable memory far below what the host-device link carries).
@@ -160,7 +182,7 @@ void finish_slot(abx_server *sv, Slot &sl)
     const abx_status st = sl.launch_rc;
     for (size_t k = 0; k < sl.reqs.size(); k++) {
         Request *r = sl.reqs[k];
-        if (st == ABX_OK && !r->on_device)
+        if (st == ABX_OK && !r->on_device && !sv->direct_host)
             par_memcpy(r->labels, sl.h_lab + sl.off[k], (size_t)r->n * sizeof(int32_t));
         finish_request(sv, r, st, t);
     }
@@ -193,7 +215,8 @@ void launch_slot(abx_server *sv, Slot &sl)
     int64_t host_pts = 0;
     for (Request *r : sl.reqs)
         host_pts += r->on_device ? 0 : r->n;
-    if (host_pts > 0 && sl.total > sl.cap) {
+    const bool stage = host_pts > 0 && !sv->direct_host;
+    if (stage && sl.total > sl.cap) {
         if (sl.h_pts)
             cudaFreeHost(sl.h_pts);
         if (sl.h_lab)
@@ -211,7 +234,7 @@ void launch_slot(abx_server *sv, Slot &sl)
     }
     void *d_pts = nullptr, *d_lab = nullptr;
     if (sl.launch_rc == ABX_OK) {
-        for (int k = 0; k < nseg; k++)
+        for (int k = 0; stage && k < nseg; k++)
             if (!sl.reqs[k]->on_device)
                 par_memcpy(sl.h_pts + 3 * sl.off[k], sl.reqs[k]->pts, (size_t)sl.reqs[k]->n * 3 * sizeof(float));
         if (sv->fault_alloc ||
@@ -231,9 +254,12 @@ void launch_slot(abx_server *sv, Slot &sl)
                 cudaEventDestroy(r->ready);  // released once the event has completed
                 r->ready = nullptr;
             }
-            cudaMemcpyAsync(dp + 3 * sl.off[k], r->on_device ? r->pts : sl.h_pts + 3 * sl.off[k],
-                            (size_t)r->n * 3 * sizeof(float),
-                            r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sl.stream);
+            if (!r->on_device && sv->direct_host)
+                copy_words(dp + 3 * sl.off[k], r->pts, 3 * r->n, sl.stream);
+            else
+                cudaMemcpyAsync(dp + 3 * sl.off[k], r->on_device ? r->pts : sl.h_pts + 3 * sl.off[k],
+                                (size_t)r->n * 3 * sizeof(float),
+                                r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sl.stream);
         }
         abx_status rc = abx_dbscan_batch(dp, sl.off.data(), nseg, sl.eps.data(), sl.minpts.data(), dl,
                                          reinterpret_cast<abx_stream>(sl.stream));
@@ -242,9 +268,12 @@ void launch_slot(abx_server *sv, Slot &sl)
         else
             for (int k = 0; k < nseg; k++) {  // and scatter the labels back
                 const Request *r = sl.reqs[k];
-                cudaMemcpyAsync(r->on_device ? r->labels : sl.h_lab + sl.off[k], dl + sl.off[k],
-                                (size_t)r->n * sizeof(int32_t),
-                                r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, sl.stream);
+                if (!r->on_device && sv->direct_host)
+                    copy_words(r->labels, dl + sl.off[k], r->n, sl.stream);
+                else
+                    cudaMemcpyAsync(r->on_device ? r->labels : sl.h_lab + sl.off[k], dl + sl.off[k],
+                                    (size_t)r->n * sizeof(int32_t),
+                                    r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, sl.stream);
             }
     }
     if (d_pts)
@@ -368,6 +397,13 @@ abx_status abx_serve_create(const abx_serve_config *cfg, abx_server **out)
     const char *f = getenv("ABX_SERVE_FAULT");
     sv->fault_hold = f && !strcmp(f, "hold");
     sv->fault_alloc = f && !strcmp(f, "alloc");
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c.device) != cudaSuccess) {
+        cudaGetLastError();
+        pageable = 0;
+    }
+    const char *st = getenv("ABX_SERVE_STAGING");  // "1": always stage host requests through pinned buffers
+    sv->direct_host = pageable == 1 && !(st && !strcmp(st, "1"));
     for (int k = 0; k < c.max_slots; k++) {
         sv->slots.emplace_back(new Slot());
         Slot &sl = *sv->slots.back();

@@ -89,7 +89,11 @@ __global__ void __launch_bounds__(256, 6) k_cand(State *__restrict__ st, const S
     int q_next = 0, q_end = 0;
     bool dry = false;
     while (true) {
+        // refill once half the warp is idle (so that a leaf's set-up runs with
+        // many lanes at once), or when every lane is
         unsigned need = __ballot_sync(~0u, !live);
+        if (__popc(need) < 16 && need != ~0u)
+            need = 0;
         while (need && !dry) {
             if (q_next >= q_end) {
                 unsigned c = 0;

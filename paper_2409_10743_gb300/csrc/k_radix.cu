@@ -207,8 +207,6 @@ constexpr size_t onesweep_smem()
 // The bucketing pass keeps each item's point (x, y, z, original index) in
 // shared memory beside its key, so the scatter reads nothing from global
 // memory; its tiles are half the radix passes' so two blocks fit an SM.
-constexpr int BUCKET_ITEMS = 16;
-constexpr int BUCKET_TILE = SORT_THREADS * BUCKET_ITEMS;
 template <typename K>
 constexpr size_t bucket_smem()
 {
@@ -220,9 +218,9 @@ constexpr size_t bucket_smem()
 // points) go to kdst and the points, with their original index, to bpts.
 
 template <bool SEG, typename K>
-__global__ void __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS)
-    k_bucket(const float *__restrict__ pts, int64_t n, State *st, const SegState *__restrict__ seg,
-             const int *__restrict__ off, K *kdst, float4 *bpts, unsigned long long *lb, unsigned *dev_status)
+__global__ void __launch_bounds__(SORT_THREADS, 4)
+    k_bucket(const float *__restrict__ pts, int64_t n, State *st, const K *__restrict__ ksrc, K *kdst, float4 *bpts,
+             unsigned long long *lb, unsigned *dev_status)
 {
     if (st->key32 != (sizeof(K) == 4))
         return;
@@ -244,8 +242,6 @@ __global__ void __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS)
     sm.wsum = s_wsum;
     __shared__ int s_tile;
 
-    const KeyGen<SEG> kg(pts, st, seg, off);
-    bool bad = false;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     while (true) {
         if (tid == 0)
@@ -264,7 +260,12 @@ __global__ void __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS)
         for (int k = 0; k < ITEMS; k++) {
             const unsigned pos = base + k * 32;
             float4 pt = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            key[k] = pos < nn ? (K)kg.key(pos, bad, pt) : (K)~(K)0;  // pads rank last and land at >= n
+            key[k] = (K)~(K)0;  // pads rank last and land at >= n
+            if (pos < nn) {
+                key[k] = ksrc[pos];
+                pt = make_float4(__ldg(pts + 3 * (size_t)pos), __ldg(pts + 3 * (size_t)pos + 1),
+                                 __ldg(pts + 3 * (size_t)pos + 2), __int_as_float((int)pos));
+            }
             s_pts[local + k * 32] = pt;
         }
         tile_rank<K, ITEMS>(key, shift, rank, sm, lb, tile, st->hist[BUCKET_ROW], dev_status);
@@ -288,8 +289,6 @@ __global__ void __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS)
         }
         __syncthreads();  // the next tile reuses the shared buffers
     }
-    if (bad)
-        atomicOr(dev_status, DEV_NONFINITE);
 }
 
 // ---- onesweep LSD pass -----------------------------------------------------------------
@@ -436,26 +435,29 @@ static void launch_sort(const Work &w, const float *points, cudaStream_t s)
     const bool try32 = w.n >= KEY32_MIN_POINTS;  // must match the allow32 given to the init kernel
     const bool bucket = w.n >= BUCKET_MIN_POINTS;
     const int g = grid_for(w, w.n, 256);
-    k_morton<SEG, u64><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[0], !bucket, bucket,
-                                         w.dev_status);
+    // with a bucketing pass the keys go to the second buffer (input order)
+    // and the bucketing pass writes them, in bucket order, to the first
+    const int kin = bucket ? 1 : 0;
+    k_morton<SEG, u64><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, w.keys[kin], 1, bucket, w.dev_status);
     if (try32)
-        k_morton<SEG, u32><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, k32[0], !bucket, bucket,
+        k_morton<SEG, u32><<<g, 256, 0, s>>>(points, w.n, w.st, w.seg, w.seg_off, k32[kin], 1, bucket,
                                              w.dev_status);
     note_launch(try32 ? 2 : 1);
     prof_mark(ST_MORTON, s);
     k_sort_plan<<<1, RADIX, 0, s>>>(w.st, w.n);
     note_launch();
-    cudaMemsetAsync(w.sort_lb, 0, (size_t)(MAX_PASSES + 1) * w.sort_tiles * RADIX * sizeof(unsigned long long), s);
+    cudaMemsetAsync(w.sort_lb, 0,
+                    ((size_t)MAX_PASSES * w.sort_tiles + w.bucket_tiles) * RADIX * sizeof(unsigned long long), s);
     if (bucket) {
-        // the bucket pass's look-back row lies past every radix pass's rows
-        unsigned long long *lb = w.sort_lb + (size_t)BUCKET_ROW * w.sort_tiles * RADIX;
+        // the bucket pass's look-back words lie past every radix pass's rows
+        unsigned long long *lb = w.sort_lb + (size_t)MAX_PASSES * w.sort_tiles * RADIX;
         const int64_t ntiles = div_up(w.n, BUCKET_TILE);
         const int t32 = (int)std::min<int64_t>(ntiles, (int64_t)g_bucket_blocks_per_sm[0] * w.n_sms);
         const int t64 = (int)std::min<int64_t>(ntiles, (int64_t)g_bucket_blocks_per_sm[1] * w.n_sms);
-        k_bucket<SEG, u64><<<t64, SORT_THREADS, bucket_smem<u64>(), s>>>(points, w.n, w.st, w.seg, w.seg_off,
-                                                                          w.keys[0], w.bpts, lb, w.dev_status);
-        k_bucket<SEG, u32><<<t32, SORT_THREADS, bucket_smem<u32>(), s>>>(points, w.n, w.st, w.seg, w.seg_off,
-                                                                          k32[0], w.bpts, lb, w.dev_status);
+        k_bucket<SEG, u64><<<t64, SORT_THREADS, bucket_smem<u64>(), s>>>(points, w.n, w.st, w.keys[1], w.keys[0],
+                                                                          w.bpts, lb, w.dev_status);
+        k_bucket<SEG, u32><<<t32, SORT_THREADS, bucket_smem<u32>(), s>>>(points, w.n, w.st, k32[1], k32[0], w.bpts,
+                                                                          lb, w.dev_status);
         note_launch(2);
     }
     const int tiles = (int)std::min<int64_t>(div_up(w.n, SORT_TILE_MIN), (int64_t)g_sort_blocks_per_sm * w.n_sms);

@@ -13,7 +13,7 @@ struct Params {
     int block;       // threads per block of the traversal kernels
     int dense_min;   // a dense cell needs at least max(minPts, 2, dense_min) points
     int schedule;    // pair traversal: 1 = candidate lists per leaf, then per point; 2 = per point
-    int digit_bits;  // radix-sort digit width (8, 10 or 11)
+    int digit_bits;  // radix-sort digit width (RADIX_BITS)
 };
 
 // Device buffers of one call; sizes are for n points (L <= n leaves).
@@ -24,7 +24,8 @@ struct Work {
     State *st;
     unsigned long long *keys[2];     // Morton keys, radix double buffer
     unsigned *vals[2];               // original indices, radix double buffer
-    unsigned long long *sort_lb;     // [MAX_PASSES + 1][tiles][RADIX] look-back words (last row: buckets)
+    unsigned long long *sort_lb;     // look-back words: [MAX_PASSES][sort_tiles][RADIX], then
+                                     // [bucket_tiles][RADIX] of the bucketing pass
     float4 *bpts;                    // [n] points in bucket order (x, y, z, original index); aliases
                                      // nodes, which are written only after the gather has read it
     unsigned long long *scan_lb;     // [scan tiles] look-back words
@@ -51,7 +52,7 @@ struct Work {
     float *seg_eps_in;               // [nseg] device copy of the caller's eps (batches)
     int *seg_minpts_in;              // [nseg] device copy of the caller's minPts (batches)
     bool any_fof, any_dbscan;        // host: which modes the call's segments use
-    size_t sort_tiles, scan_tiles;
+    size_t sort_tiles, scan_tiles, bucket_tiles;
 };
 
 size_t work_bytes(int64_t n, int nseg = 1);

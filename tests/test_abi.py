@@ -69,7 +69,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.abx_dbscan_ex(fake, 10, 0.1, 2, fake, ctypes.byref(bad), null) == ABX_EINVAL
     bad = Params(dense_cells=2)
     assert lib.abx_dbscan_ex(fake, 10, 0.1, 2, fake, ctypes.byref(bad), null) == ABX_EINVAL
-    for bad in (Params(schedule=3), Params(schedule=-1), Params(sort_digit_bits=9), Params(sort_digit_bits=12)):
+    for bad in (Params(schedule=3), Params(schedule=-1), Params(sort_digit_bits=9), Params(sort_digit_bits=10),
+                Params(sort_digit_bits=12)):
         assert lib.abx_dbscan_ex(fake, 10, 0.1, 2, fake, ctypes.byref(bad), null) == ABX_EINVAL
 
 

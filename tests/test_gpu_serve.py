@@ -36,7 +36,12 @@ def _alone(abx, p, eps, minpts):
     return abx.dbscan(torch.from_numpy(p).cuda(), eps, minpts).cpu().numpy()
 
 
-def test_results_equal_alone_and_oracle(abx, requests):
+@pytest.mark.parametrize("staging", ["0", "1"], ids=["direct-host-access", "pinned-staging"])
+def test_results_equal_alone_and_oracle(abx, requests, staging, monkeypatch):
+    """Host-resident requests, moved either by copy kernels that address the
+    host's pageable memory (where the GPU shares its page tables) or through
+    pinned staging buffers (ABX_SERVE_STAGING=1, and everywhere else)."""
+    monkeypatch.setenv("ABX_SERVE_STAGING", staging)
     srv = abx.Server(max_slots=2, max_batch_requests=16)
     try:
         tickets = [srv.submit(p, r.eps, r.minpts) for r, p in requests[:24]]   # a burst
