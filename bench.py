@@ -51,6 +51,8 @@ def stage_bytes(stage: str, c: dict, n: int) -> float:
     table = {
         "bounds": 12.0,                                   # read xyz
         "morton": 12.0 + kb,                              # read xyz, write key
+        # inputs above 2^23 points: key + point in, key + (point, index) out, by the key's top bits
+        "bucket": (kb + 12.0 + kb + 16.0) if n >= (1 << 23) else 0.0,
         "sort": (kb + kb + 4.0) + (P - 1) * 2 * (kb + 4.0),  # 1st pass: key in, key+idx out; then both ways
         "gather": 4.0 + 12.0 + 16.0,                      # perm, xyz, sorted float4 (the union-find
                                                           # resets are charged to the traversal's parent RMW)

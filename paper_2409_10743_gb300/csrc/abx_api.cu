@@ -579,7 +579,7 @@ abx_status abx_selftest_wait_timeout(int32_t spin_limit, abx_stream stream)
     return cuda_status(cudaGetLastError());
 }
 
-static const char *k_stage_names[ST_NUM] = {"bounds", "morton", "sort", "gather", "cells", "leaves",
+static const char *k_stage_names[ST_NUM] = {"bounds", "morton", "bucket", "sort", "gather", "cells", "leaves",
                                            "build", "candidates", "count", "union", "border", "finalize"};
 
 abx_status abx_profile_enable(int32_t on)

@@ -86,8 +86,8 @@ struct abx_server {
     size_t bytes_in_use = 0, peak_bytes = 0;
     bool stop = false;
     bool fault_hold = false, fault_alloc = false;
-    bool direct_host = false;  // kernels may read and write pageable host memory
-                               // (cudaDevAttrPageableMemoryAccess): no staging copies
+    bool stage_points = false;  // host points through pinned staging (ABX_SERVE_STAGING=1)
+                                // instead of straight from the caller's memory
     // statistics
     uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, batches = 0, batched_requests = 0;
     std::vector<double> latencies;
@@ -95,26 +95,6 @@ struct abx_server {
 };
 
 namespace {
-
-// Where the GPU can address pageable host memory (systems whose GPU shares
-// the host's page tables), a host request's points are read and its labels
-// written by these copies on the slot's stream, asynchronous like the rest of
-// the batch; elsewhere they go through pinned staging buffers.
-__global__ void __launch_bounds__(256) k_copy_words(unsigned *__restrict__ dst, const unsigned *__restrict__ src,
-                                                    int64_t n)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[i];
-}
-
-void copy_words(void *dst, const void *src, int64_t words, cudaStream_t s)
-{
-    if (words <= 0)
-        return;
-    const int64_t g = std::min<int64_t>((words + 255) / 256, 152 * 16);
-    k_copy_words<<<(int)g, 256, 0, s>>>(static_cast<unsigned *>(dst), static_cast<const unsigned *>(src), words);
-    note_launch();
-}
 
 // Host copies of large staging buffers are split over a few threads (one core
 // copies pageable memory far below what the host-device link carries).
@@ -182,7 +162,7 @@ void finish_slot(abx_server *sv, Slot &sl)
     const abx_status st = sl.launch_rc;
     for (size_t k = 0; k < sl.reqs.size(); k++) {
         Request *r = sl.reqs[k];
-        if (st == ABX_OK && !r->on_device && !sv->direct_host)
+        if (st == ABX_OK && !r->on_device)
             par_memcpy(r->labels, sl.h_lab + sl.off[k], (size_t)r->n * sizeof(int32_t));
         finish_request(sv, r, st, t);
     }
@@ -215,7 +195,10 @@ void launch_slot(abx_server *sv, Slot &sl)
     int64_t host_pts = 0;
     for (Request *r : sl.reqs)
         host_pts += r->on_device ? 0 : r->n;
-    const bool stage = host_pts > 0 && !sv->direct_host;
+    // labels of host requests come back through pinned memory (a copy into
+    // pageable memory would wait for the batch); points are copied from the
+    // caller's memory by the driver, or staged here with ABX_SERVE_STAGING=1
+    const bool stage = host_pts > 0;
     if (stage && sl.total > sl.cap) {
         if (sl.h_pts)
             cudaFreeHost(sl.h_pts);
@@ -224,17 +207,20 @@ void launch_slot(abx_server *sv, Slot &sl)
         sl.h_pts = nullptr;
         sl.h_lab = nullptr;
         sl.cap = 0;
-        if (cudaMallocHost((void **)&sl.h_pts, (size_t)sl.total * 3 * sizeof(float)) != cudaSuccess ||
-            cudaMallocHost((void **)&sl.h_lab, (size_t)sl.total * sizeof(int32_t)) != cudaSuccess) {
+        // once, at the batch size limit: pinning memory takes long enough to
+        // show in the latency of the batch that would wait for it
+        const int64_t cap = std::max<int64_t>(sl.total, sv->cfg.max_batch_points);
+        if ((sv->stage_points && cudaMallocHost((void **)&sl.h_pts, (size_t)cap * 3 * sizeof(float)) != cudaSuccess) ||
+            cudaMallocHost((void **)&sl.h_lab, (size_t)cap * sizeof(int32_t)) != cudaSuccess) {
             cudaGetLastError();
             sl.launch_rc = ABX_ENOMEM;
         } else {
-            sl.cap = sl.total;
+            sl.cap = cap;
         }
     }
     void *d_pts = nullptr, *d_lab = nullptr;
     if (sl.launch_rc == ABX_OK) {
-        for (int k = 0; stage && k < nseg; k++)
+        for (int k = 0; stage && sv->stage_points && k < nseg; k++)
             if (!sl.reqs[k]->on_device)
                 par_memcpy(sl.h_pts + 3 * sl.off[k], sl.reqs[k]->pts, (size_t)sl.reqs[k]->n * 3 * sizeof(float));
         if (sv->fault_alloc ||
@@ -254,12 +240,9 @@ void launch_slot(abx_server *sv, Slot &sl)
                 cudaEventDestroy(r->ready);  // released once the event has completed
                 r->ready = nullptr;
             }
-            if (!r->on_device && sv->direct_host)
-                copy_words(dp + 3 * sl.off[k], r->pts, 3 * r->n, sl.stream);
-            else
-                cudaMemcpyAsync(dp + 3 * sl.off[k], r->on_device ? r->pts : sl.h_pts + 3 * sl.off[k],
-                                (size_t)r->n * 3 * sizeof(float),
-                                r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sl.stream);
+            const float *src = r->on_device || !sv->stage_points ? r->pts : sl.h_pts + 3 * sl.off[k];
+            cudaMemcpyAsync(dp + 3 * sl.off[k], src, (size_t)r->n * 3 * sizeof(float),
+                            r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sl.stream);
         }
         abx_status rc = abx_dbscan_batch(dp, sl.off.data(), nseg, sl.eps.data(), sl.minpts.data(), dl,
                                          reinterpret_cast<abx_stream>(sl.stream));
@@ -268,12 +251,9 @@ void launch_slot(abx_server *sv, Slot &sl)
         else
             for (int k = 0; k < nseg; k++) {  // and scatter the labels back
                 const Request *r = sl.reqs[k];
-                if (!r->on_device && sv->direct_host)
-                    copy_words(r->labels, dl + sl.off[k], r->n, sl.stream);
-                else
-                    cudaMemcpyAsync(r->on_device ? r->labels : sl.h_lab + sl.off[k], dl + sl.off[k],
-                                    (size_t)r->n * sizeof(int32_t),
-                                    r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, sl.stream);
+                cudaMemcpyAsync(r->on_device ? r->labels : sl.h_lab + sl.off[k], dl + sl.off[k],
+                                (size_t)r->n * sizeof(int32_t),
+                                r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, sl.stream);
             }
     }
     if (d_pts)
@@ -397,13 +377,8 @@ abx_status abx_serve_create(const abx_serve_config *cfg, abx_server **out)
     const char *f = getenv("ABX_SERVE_FAULT");
     sv->fault_hold = f && !strcmp(f, "hold");
     sv->fault_alloc = f && !strcmp(f, "alloc");
-    int pageable = 0;
-    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c.device) != cudaSuccess) {
-        cudaGetLastError();
-        pageable = 0;
-    }
-    const char *st = getenv("ABX_SERVE_STAGING");  // "1": always stage host requests through pinned buffers
-    sv->direct_host = pageable == 1 && !(st && !strcmp(st, "1"));
+    const char *st = getenv("ABX_SERVE_STAGING");  // "1": stage host points through pinned buffers
+    sv->stage_points = st && !strcmp(st, "1");
     for (int k = 0; k < c.max_slots; k++) {
         sv->slots.emplace_back(new Slot());
         Slot &sl = *sv->slots.back();

@@ -28,8 +28,6 @@ struct Tree {
     const float4 *__restrict__ nodes;
     const int *__restrict__ leaf_first;
     int L;
-    const State *st = nullptr;     // with the sorted keys: split levels between any two points
-    const void *k0 = nullptr, *k1 = nullptr;
 };
 
 // A traversal visits every node at most once; a node index outside the
@@ -276,7 +274,7 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
             }
         }
     };
-    bool may_exit = SCHED == 2;
+    constexpr bool may_exit = SCHED == 2;
     if (SCHED == 1) {
         for (int c = 0; c < CAND_SLOTS; c++) {
             const int v = c == 0 ? c4.y : c == 1 ? c4.z : c4.w;
@@ -284,18 +282,6 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
                 break;
             if (v < 0) {  // more candidates than the list holds: walk on from there
                 node = -v - 2;
-                // The early exit needs the highest split level crossed since
-                // i's leaf: that of the leaf boundaries between i's leaf and
-                // the resume leaf, which is the split level between the keys
-                // of the last point of the one and the first of the other
-                // (the highest differing bit of two sorted keys is the
-                // highest of those of the neighbouring pairs between them).
-                const int last_own = (own_end & ~(int)DENSE_BIT) - 1;
-                const int first = (int)(__float_as_uint(__ldg(T.nodes + 2 * (size_t)node).w) & ~DENSE_BIT);
-                M = split_level(sorted_key(T.st, T.k0, T.k1, last_own), sorted_key(T.st, T.k0, T.k1, first),
-                                last_own);
-                H = reach_level(p.x, p.y, p.z, p.x, p.y, p.z, g);
-                may_exit = true;
                 break;
             }
             // the leaf passed the leaf-box test; the point's own box test is
@@ -307,8 +293,9 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
         }
     }
     // the plain pair traversal: from i's own leaf (SCHED 2) or from the leaf
-    // where the candidate list ran out (SCHED 1, without the early exit: the
-    // levels crossed before that leaf are not known here)
+    // where the candidate list ran out (SCHED 1, without the early exit: it
+    // would need the levels crossed before that leaf, and on dense data, where
+    // lists overflow, it rarely fires; measured, it slowed this loop down)
     unsigned steps = 0;
     while (node != SENTINEL) {
         if (!node_ok(node, L, steps, dev_status))
@@ -357,7 +344,7 @@ __global__ void __launch_bounds__(1024, 2) k_union(int64_t n, const State *__res
     const int i = (int)i64;
     if (!FOF && !core[i])
         return;
-    const Tree T{nodes, leaf_first, st->n_leaves, st, k0, k1};
+    const Tree T{nodes, leaf_first, st->n_leaves};
     union_query<SCHED, FOF, STATS>(i, seg[0], T, spts, leaf_of, cand, parent, core, dev_status, stats);
 }
 
@@ -375,7 +362,7 @@ __global__ void __launch_bounds__(1024, 2) k_union_seg(int64_t n, const State *_
         return;
     const int i = (int)i64;
     const SegState &g = seg[seg_of_key(sorted_key(st, k0, k1, i), st->shift)];
-    const Tree T{nodes, leaf_first, st->n_leaves, st, k0, k1};
+    const Tree T{nodes, leaf_first, st->n_leaves};
     if (g.minpts <= 2)
         union_query<SCHED, true, STATS>(i, g, T, spts, leaf_of, cand, parent, core, dev_status, stats);
     else if (core[i])

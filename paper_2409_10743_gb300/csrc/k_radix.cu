@@ -460,6 +460,7 @@ static void launch_sort(const Work &w, const float *points, cudaStream_t s)
                                                                           lb, w.dev_status);
         note_launch(2);
     }
+    prof_mark(ST_BUCKET, s);  // (with the sort plan and the look-back reset)
     const int tiles = (int)std::min<int64_t>(div_up(w.n, SORT_TILE_MIN), (int64_t)g_sort_blocks_per_sm * w.n_sms);
     for (int pass = 0; pass < MAX_PASSES; pass++)
         k_onesweep<u64><<<tiles, SORT_THREADS, onesweep_smem<u64>(), s>>>(pass, w.keys[0], w.keys[1], w.vals[0],

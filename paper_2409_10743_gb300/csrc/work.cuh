@@ -93,7 +93,7 @@ void cluster_init_device();
 // Stage timers and launch accounting (profile mode records a CUDA event on the
 // launching stream at each stage boundary).
 enum Stage {
-    ST_BOUNDS = 0, ST_MORTON, ST_SORT, ST_GATHER, ST_CELLS, ST_LEAVES, ST_BUILD,
+    ST_BOUNDS = 0, ST_MORTON, ST_BUCKET, ST_SORT, ST_GATHER, ST_CELLS, ST_LEAVES, ST_BUILD,
     ST_CANDS, ST_COUNT, ST_UNION, ST_BORDER, ST_FINALIZE, ST_NUM
 };
 void prof_begin(cudaStream_t s);

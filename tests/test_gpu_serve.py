@@ -36,11 +36,10 @@ def _alone(abx, p, eps, minpts):
     return abx.dbscan(torch.from_numpy(p).cuda(), eps, minpts).cpu().numpy()
 
 
-@pytest.mark.parametrize("staging", ["0", "1"], ids=["direct-host-access", "pinned-staging"])
+@pytest.mark.parametrize("staging", ["0", "1"], ids=["from-caller-memory", "pinned-staging"])
 def test_results_equal_alone_and_oracle(abx, requests, staging, monkeypatch):
-    """Host-resident requests, moved either by copy kernels that address the
-    host's pageable memory (where the GPU shares its page tables) or through
-    pinned staging buffers (ABX_SERVE_STAGING=1, and everywhere else)."""
+    """Host-resident requests, their points copied straight from the caller's
+    memory or staged through pinned buffers (ABX_SERVE_STAGING=1)."""
     monkeypatch.setenv("ABX_SERVE_STAGING", staging)
     srv = abx.Server(max_slots=2, max_batch_requests=16)
     try:
