@@ -357,13 +357,15 @@ __device__ __forceinline__ int uf_find(int *parent, int x)
     }
 }
 
-__device__ __forceinline__ void uf_unite(int *parent, const float4 *pts, int a, int b)
+// Merge the sets of a and b; returns the root that the merged set had when
+// the call ended (a member of it ever after: sets only grow).
+__device__ __forceinline__ int uf_unite(int *parent, const float4 *pts, int a, int b)
 {
     while (true) {
         a = uf_find(parent, a);
         b = uf_find(parent, b);
         if (a == b)
-            return;
+            return a;
         // strict total order (original index, position): chains never cycle
         const int oa = orig_of(pts, a), ob = orig_of(pts, b);
         if (oa > ob || (oa == ob && a > b)) {
@@ -374,7 +376,7 @@ __device__ __forceinline__ void uf_unite(int *parent, const float4 *pts, int a, 
         // hook b (larger priority) under a
         int old = atomicCAS(parent + b, b, a);
         if (old == b)
-            return;
+            return a;
         b = old;
     }
 }

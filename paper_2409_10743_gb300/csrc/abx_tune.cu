@@ -103,7 +103,17 @@ static abx_status search(const std::function<abx_status(const abx_params &)> &ru
         {3, [&](abx_params &p, int k) { p.dense_cells = denses[k][0], p.dense_min = denses[k][1]; }},
         {2, [&](abx_params &p, int k) { p.schedule = schedules[k]; }},
     };
+    // start from the library defaults, spelled out, so that every field of
+    // the pick is explicit even where no candidate beat them
+    Params d;
+    resolve_params(nullptr, d);
     abx_params cur{};
+    cur.leaf_size = d.leaf_size;
+    cur.dense_cells = d.dense ? 1 : -1;
+    cur.block = d.block;
+    cur.dense_min = d.dense_min;
+    cur.schedule = d.schedule;
+    cur.sort_digit_bits = d.digit_bits;
     float cur_ms = INFINITY;
     abx_status rc = ABX_OK;
     for (const Axis &ax : axes) {

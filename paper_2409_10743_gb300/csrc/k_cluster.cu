@@ -60,6 +60,7 @@ __device__ __forceinline__ bool node_ok(int node, int L, unsigned &steps, unsign
 
 constexpr int CAND_SLOTS = 3;
 constexpr int CAND_TICKETS = MAX_PASSES + 3;  // tile_ctr index of the candidate pass's leaf queue
+constexpr int CAND_CHUNK = 64;                // leaves a warp takes from the queue at a time
 static int g_cand_blocks_per_sm = 4;           // set per process by cluster_init_device
 
 // Persistent: the walks differ in length by an order of magnitude, and a warp
@@ -96,14 +97,14 @@ __global__ void __launch_bounds__(256, 6) k_cand(State *__restrict__ st, const S
             if (q_next >= q_end) {
                 unsigned c = 0;
                 if (lane == 0)
-                    c = atomicAdd(queue, 32u);
+                    c = atomicAdd(queue, (unsigned)CAND_CHUNK);
                 c = __shfl_sync(~0u, c, 0);
                 if (c >= (unsigned)L) {
                     dry = true;
                     break;
                 }
                 q_next = (int)c;
-                q_end = (int)min(c + 32u, (unsigned)L);
+                q_end = (int)min(c + (unsigned)CAND_CHUNK, (unsigned)L);
             }
             const int avail = q_end - q_next;
             const int r = __popc(need & lt);
@@ -142,10 +143,7 @@ __global__ void __launch_bounds__(256, 6) k_cand(State *__restrict__ st, const S
                 if (node < L - 1) {
                     node = __float_as_int(lo.w);
                     descend = true;
-                } else if (k == CAND_SLOTS) {  // a fourth: resume at the third one's node
-                    out2 = -((L - 1 + out2) + 2);
-                    fin = true;
-                } else {
+                } else if (k < CAND_SLOTS) {
                     const int t = node - (L - 1);
                     if (k == 0)
                         out0 = t;
@@ -154,6 +152,9 @@ __global__ void __launch_bounds__(256, 6) k_cand(State *__restrict__ st, const S
                     else
                         out2 = t;
                     k++;
+                } else {  // a fourth: resume at the third one's node
+                    out2 = -((L - 1 + out2) + 2);
+                    fin = true;
                 }
             }
             if (!descend && !fin) {
@@ -192,7 +193,8 @@ struct TravStats {
 template <int SCHED, bool FOF, bool STATS>
 __device__ __forceinline__ void union_query(const int i, const SegState &g, const Tree &T,
                                             const float4 *__restrict__ spts, const int *__restrict__ leaf_of,
-                                            const int4 *__restrict__ cand, int *parent, unsigned char *core, unsigned *dev_status, TravStats *stats)
+                                            const int4 *__restrict__ cand, int *parent, unsigned char *core,
+                                            unsigned *dev_status, TravStats *stats)
 {
     const int L = T.L;
     const float e2 = g.e2;
@@ -216,6 +218,14 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
         M = level_of(ahi);
         node = region_exit(M, 0, H) ? SENTINEL : __float_as_int(ahi.w);
     }
+    // ri: a member of i's set, its root when last seen.  Sets only grow, so a
+    // neighbour whose parent is ri is in i's set already: one load, no finds
+    // (on dense data most neighbour pairs are such repeats)
+    int ri = i;
+    auto link = [&](const int j) {
+        if (ld_cg(parent + j) != ri)
+            ri = uf_unite(parent, spts, ri, j);
+    };
     if (own_end >= 0) {  // not a dense cell (its points are one set already)
         const int e = own_end;
         for (int j = i + 1; j < e; j++) {
@@ -223,7 +233,7 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
             if (STATS)
                 c_test++;
             if ((FOF || core[j]) && dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
-                uf_unite(parent, spts, i, j);
+                link(j);
                 if (STATS)
                     c_union++;
                 if (FOF) {
@@ -241,7 +251,9 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
         if (lw & DENSE_BIT) {
             // all points of a dense cell are core and already one set:
             // one link is enough, none if i is already in that set
-            if (uf_find(parent, i) == uf_find(parent, s)) {
+            const int rs = uf_find(parent, s);
+            ri = uf_find(parent, ri);
+            if (ri == rs) {
                 found = true;
                 return;
             }
@@ -250,7 +262,7 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
                 if (STATS)
                     c_test++;
                 if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
-                    uf_unite(parent, spts, i, s);
+                    ri = uf_unite(parent, spts, ri, rs);
                     if (STATS)
                         c_union++;
                     found = true;
@@ -264,7 +276,7 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
             if (STATS)
                 c_test++;
             if ((FOF || core[j]) && dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
-                uf_unite(parent, spts, i, j);
+                link(j);
                 if (STATS)
                     c_union++;
                 if (FOF) {
@@ -276,21 +288,31 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
     };
     constexpr bool may_exit = SCHED == 2;
     if (SCHED == 1) {
+        // The list holds leaves (>= 0) in rope order, then SENTINEL; the
+        // third slot may instead hold -(node + 2): more candidates than the
+        // list holds, walk on from that node.  Each listed leaf passed the
+        // leaf-box test; the point's own box test is tighter and spares the
+        // point tests of most far leaves.  The boxes are loaded first, all at
+        // once (independent loads), then tested.
+        const int v[CAND_SLOTS] = {c4.y, c4.z, c4.w};
+        unsigned hit = 0, lw[CAND_SLOTS];
+#pragma unroll
         for (int c = 0; c < CAND_SLOTS; c++) {
-            const int v = c == 0 ? c4.y : c == 1 ? c4.z : c4.w;
-            if (v == SENTINEL)
-                break;
-            if (v < 0) {  // more candidates than the list holds: walk on from there
-                node = -v - 2;
-                break;
+            lw[c] = 0;
+            if (v[c] >= 0) {
+                float4 lo, hi;
+                ld_node(T.nodes, L - 1 + v[c], lo, hi);
+                lw[c] = __float_as_uint(lo.w);
+                if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2)
+                    hit |= 1u << c;
             }
-            // the leaf passed the leaf-box test; the point's own box test is
-            // tighter and spares the point tests of most far leaves
-            float4 lo, hi;
-            ld_node(T.nodes, L - 1 + v, lo, hi);
-            if (box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2)
-                test_leaf(__float_as_uint(lo.w), leaf_first[v + 1]);
         }
+#pragma unroll
+        for (int c = 0; c < CAND_SLOTS; c++)
+            if ((hit >> c) & 1u)
+                test_leaf(lw[c], leaf_first[v[c] + 1]);
+        if (c4.w < SENTINEL)
+            node = -c4.w - 2;
     }
     // the plain pair traversal: from i's own leaf (SCHED 2) or from the leaf
     // where the candidate list ran out (SCHED 1, without the early exit: it
@@ -396,7 +418,7 @@ __global__ void k_count(int64_t n, const State *__restrict__ st, const SegState 
                         const unsigned long long *k0, const unsigned long long *k1,
                         const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
                         const int *__restrict__ leaf_first, const int *__restrict__ leaf_of,
-                        unsigned char *core, unsigned *dev_status)
+                        const int4 *__restrict__ cand, unsigned char *core, unsigned *dev_status)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i64 >= n)
@@ -415,8 +437,44 @@ __global__ void k_count(int64_t n, const State *__restrict__ st, const SegState 
     const Tree T{nodes, leaf_first, st->n_leaves};
     const int L = T.L;
     const float4 p = spts[i];
-    RootWalkExit ex{L - 1 + leaf_of[i], reach_level(p.x, p.y, p.z, p.x, p.y, p.z, g), 0, false};
+    const int me = leaf_of[i];
     int cnt = 0;
+    if (cand) {
+        // Lower bound first: the own leaf's points (i itself among them) and
+        // those of the listed candidate leaves (all after the own leaf in
+        // pre-order, so none is counted twice).  Enough of them settle most
+        // core points in dense data without the walk from the root.
+        auto count_leaf = [&](int s0, int e) -> bool {
+            for (int j = s0; j < e; j++) {
+                const float4 q = __ldg(spts + j);
+                if (dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2 && ++cnt >= minpts)
+                    return true;
+            }
+            return false;
+        };
+        auto count_listed = [&](int v) -> bool {
+            float4 lo, hi;
+            ld_node(nodes, L - 1 + v, lo, hi);
+            return box_dist2_rn(p.x, p.y, p.z, lo, hi) <= e2 &&
+                   count_leaf((int)(__float_as_uint(lo.w) & ~DENSE_BIT), leaf_first[v + 1]);
+        };
+        const int4 c4 = cand[me];
+        bool core_found = count_leaf(leaf_first[me], c4.x & ~DENSE_BIT);
+        const int v[3] = {c4.y, c4.z, c4.w};
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            ok = ok && v[c] >= 0;
+            if (ok && !core_found)
+                core_found = count_listed(v[c]);
+        }
+        if (core_found) {
+            core[i] = 1;
+            return;
+        }
+        cnt = 0;  // the full count walks the whole hierarchy
+    }
+    RootWalkExit ex{L - 1 + me, reach_level(p.x, p.y, p.z, p.x, p.y, p.z, g), 0, false};
     int node = g.root;
     unsigned steps = 0;
     while (node != SENTINEL) {
@@ -612,12 +670,13 @@ void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t
     }
     prof_mark(ST_CANDS, s);
     if (w.any_dbscan) {
+        const int4 *lists = p.schedule == 1 ? w.cand : nullptr;  // k_cand's lists, if it ran
         if (seg)
             k_count<true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
-                                          w.leaf_of, w.core, w.dev_status);
+                                          w.leaf_of, lists, w.core, w.dev_status);
         else
             k_count<false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes, w.leaf_first,
-                                           w.leaf_of, w.core, w.dev_status);
+                                           w.leaf_of, lists, w.core, w.dev_status);
         note_launch();
         prof_mark(ST_COUNT, s);
     }

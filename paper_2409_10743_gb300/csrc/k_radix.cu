@@ -116,16 +116,15 @@ struct TileSmem {
 };
 
 // Ranks the tile's keys by the digit (key >> shift) & (RADIX - 1), stable in
-// item order (warp by warp, item by item, lane by lane), and finds where each
-// digit's run goes: the tile publishes its digit counts in its row of the
-// look-back array `lb` and adds up those of the tiles before it.  After the
-// call, item k of this thread goes to tile position
-//   sm.loc[d] + sm.whist[warp][d] + rank[k]
-// and to output position sm.glob[d] + (tile position).
+// item order (warp by warp, item by item, lane by lane), and publishes the
+// tile's digit counts in its row of the look-back array `lb`.  After the call
+// (it ends with a barrier), item k of this thread goes to tile position
+//   sm.loc[d] + sm.whist[warp][d] + rank[k].
+// Returns the tile's count of digit d = threadIdx.x (threads below RADIX),
+// which tile_place needs.
 template <typename K, int ITEMS>
-__device__ __forceinline__ void tile_rank(const K (&key)[ITEMS], int shift, unsigned (&rank)[ITEMS],
-                                          const TileSmem &sm, unsigned long long *lb, int tile,
-                                          const unsigned *digit_base, unsigned *dev_status)
+__device__ __forceinline__ unsigned tile_rank(const K (&key)[ITEMS], int shift, unsigned (&rank)[ITEMS],
+                                              const TileSmem &sm, unsigned long long *lb, int tile)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // stable rank within the warp: lanes with equal digit, in lane order, after
@@ -152,9 +151,9 @@ __device__ __forceinline__ void tile_rank(const K (&key)[ITEMS], int shift, unsi
     }
     __syncthreads();
 
-    // thread d < RADIX: per-warp exclusive offsets and the tile count of digit d
+    // thread d < RADIX: per-warp exclusive offsets and the tile count of digit
+    // d, published at once (inclusive of the tiles before only for tile 0)
     unsigned cnt = 0;
-    unsigned long long excl = 0;
     if (tid < RADIX) {
         const int d = tid;
 #pragma unroll
@@ -163,14 +162,7 @@ __device__ __forceinline__ void tile_rank(const K (&key)[ITEMS], int shift, unsi
             sm.whist[w * RADIX + d] = cnt;
             cnt += c;
         }
-        // publish, then look back
-        if (tile == 0) {
-            lb_store(lb + d, LB_FLAG_PRE | cnt);
-        } else {
-            lb_store(lb + (size_t)tile * RADIX + d, LB_FLAG_AGG | cnt);
-            excl = lookback<8>(lb, tile, RADIX, tid, dev_status);
-            lb_store(lb + (size_t)tile * RADIX + d, LB_FLAG_PRE | (excl + cnt));
-        }
+        lb_store(lb + (size_t)tile * RADIX + d, (tile == 0 ? LB_FLAG_PRE : LB_FLAG_AGG) | cnt);
     }
     // exclusive scan of cnt over digits (tile-local offsets)
     unsigned x = cnt;
@@ -187,9 +179,28 @@ __device__ __forceinline__ void tile_rank(const K (&key)[ITEMS], int shift, unsi
         unsigned wpre = 0;
         for (int w = 0; w < warp; w++)
             wpre += sm.wsum[w];
-        const unsigned loc = wpre + x - cnt;
-        sm.loc[tid] = loc;
-        sm.glob[tid] = digit_base[tid] + (unsigned)excl - loc;
+        sm.loc[tid] = wpre + x - cnt;
+    }
+    __syncthreads();
+    return cnt;
+}
+
+// Where the tile's run of each digit goes: sm.glob[d] + (tile position) is
+// the output position.  Adds up the counts of the tiles before this one
+// (decoupled look-back) and publishes the inclusive counts.  Called once the
+// tile's items are in shared memory, so that the wait overlaps that work and
+// the items' registers are free; ends with a barrier.
+__device__ __forceinline__ void tile_place(unsigned cnt, const TileSmem &sm, unsigned long long *lb, int tile,
+                                           const unsigned *digit_base, unsigned *dev_status)
+{
+    const int tid = threadIdx.x;
+    if (tid < RADIX) {
+        unsigned long long excl = 0;
+        if (tile > 0) {
+            excl = lookback<8>(lb, tile, RADIX, tid, dev_status);
+            lb_store(lb + (size_t)tile * RADIX + tid, LB_FLAG_PRE | (excl + cnt));
+        }
+        sm.glob[tid] = digit_base[tid] + (unsigned)excl - sm.loc[tid];
     }
     __syncthreads();
 }
@@ -268,7 +279,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4)
             }
             s_pts[local + k * 32] = pt;
         }
-        tile_rank<K, ITEMS>(key, shift, rank, sm, lb, tile, st->hist[BUCKET_ROW], dev_status);
+        const unsigned cnt = tile_rank<K, ITEMS>(key, shift, rank, sm, lb, tile);
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             const unsigned dd = (unsigned)(key[k] >> shift) & (RADIX - 1);
@@ -276,7 +287,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4)
             s_keys[lp] = key[k];
             s_src[lp] = (unsigned short)(local + k * 32);
         }
-        __syncthreads();
+        tile_place(cnt, sm, lb, tile, st->hist[BUCKET_ROW], dev_status);
 #pragma unroll 4
         for (int i = tid; i < TILE; i += SORT_THREADS) {
             const K kk = s_keys[i];
@@ -341,27 +352,24 @@ __global__ void __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS)
         // positions fit 32 bits: n < 2^31 and a tile ends at most TILE - 1 past n
         const unsigned base = (unsigned)tile * TILE + (unsigned)warp * 32 * ITEMS + lane;
         K key[ITEMS];
-        unsigned val[ITEMS];
         unsigned rank[ITEMS];
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             const unsigned pos = base + k * 32;
             key[k] = pos < nn ? ksrc[pos] : (K)~(K)0;  // pads rank last in digit RADIX-1 and land at >= n
         }
+        const unsigned cnt = tile_rank<K, ITEMS>(key, shift, rank, sm, lb, tile);
+        // the values are read only now, straight into their places: they
+        // hold no registers through the ranking
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             const unsigned pos = base + k * 32;
-            val[k] = pos < nn ? (first ? pos : vsrc[pos]) : 0u;
-        }
-        tile_rank<K, ITEMS>(key, shift, rank, sm, lb, tile, st->hist[pass], dev_status);
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
             const unsigned dd = (unsigned)(key[k] >> shift) & (RADIX - 1);
             const unsigned lp = sm.loc[dd] + sm.whist[warp * RADIX + dd] + rank[k];
             s_keys[lp] = key[k];
-            s_vals[lp] = val[k];
+            s_vals[lp] = pos < nn ? (first ? pos : vsrc[pos]) : 0u;
         }
-        __syncthreads();
+        tile_place(cnt, sm, lb, tile, st->hist[pass], dev_status);
 #pragma unroll 4
         for (int i = tid; i < TILE; i += SORT_THREADS) {
             const K kk = s_keys[i];

@@ -137,3 +137,25 @@ def test_batch_schedules_and_batch_tuner(abx):
     got = abx.dbscan_batch(t, off, eps, mp)
     torch.cuda.synchronize()
     assert np.array_equal(got.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("kw", [dict(leaf_size=1, dense_cells=-1), dict(leaf_size=2, dense_cells=-1), dict(leaf_size=4)],
+                         ids=["leaf1", "leaf2", "dense-leaf4"])
+@pytest.mark.parametrize("minpts", [3, 12, 40])
+def test_dbscan_count_from_lists_and_list_overflow(abx, kw, minpts):
+    """The core count first counts the own leaf and the listed candidate
+    leaves and walks from the root only when they hold fewer than minPts
+    neighbours; the union walks on where a list overflowed.  Over this range
+    of eps (from a few clustered points to 90%) the lists run from empty to
+    overflowing and the count from settled by the lists to needing the walk."""
+    from workloads import clumps
+    p = clumps(40_000, 30, 913 + minpts, a0=0.004)
+    for eps in (0.002, 0.005, 0.012, 0.03):
+        check(abx, p, eps, minpts, abx.Params(schedule=1, **kw), f"{kw} eps={eps}")
+    abx.profile_enable(2)
+    try:
+        labels_of(abx, p, 0.03, minpts, abx.Params(schedule=1, **kw))
+        tr = abx.profile_traversal()
+    finally:
+        abx.profile_enable(False)
+    assert tr["queries"] > 0 and tr["visits"] > 0, tr  # some lists overflowed
