@@ -478,10 +478,12 @@ static int grid_cap(const Work &w, int64_t n, int block, int per_sm = 8)
 void stage_cells_leaves(const Work &w, const Params &p, cudaStream_t s)
 {
     const int scan_tiles = div_up(w.n, SCAN_TILE);
-    cudaMemsetAsync(w.dense_root, 0xff, (size_t)w.n * sizeof(int), s);
-    k_dense_cells<<<grid_cap(w, w.n, 256, 16), 256, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts,
-                                                            w.dense_root, p.dense_min);
-    note_launch(1);
+    if (p.dense) {  // (with dense cells off no segment is dense_ok, and nothing reads dense_root)
+        cudaMemsetAsync(w.dense_root, 0xff, (size_t)w.n * sizeof(int), s);
+        k_dense_cells<<<grid_cap(w, w.n, 256, 16), 256, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts,
+                                                                w.dense_root, p.dense_min);
+        note_launch(1);
+    }
     prof_mark(ST_CELLS, s);
     cudaMemsetAsync(w.scan_lb, 0, w.scan_tiles * sizeof(unsigned long long), s);
     LeafFlag lf{w.dense_root, w.pdelta, w.parent, w.core, w.st, w.keys[0], w.keys[1], p.leaf_size, w.n};

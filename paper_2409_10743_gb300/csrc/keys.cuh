@@ -1,5 +1,5 @@
-// Morton keys of the input points, shared by the histogram pass and the
-// bucketing pass (which recomputes them instead of reading them back).
+// Morton keys of the input points (the histogram pass computes and writes
+// them).
 //
 // key = segment << shift | Morton code (shift = 3 * the widest per-axis width),
 // so segments sort apart and each forms its own subtree.  Each axis is
@@ -15,14 +15,13 @@ namespace abx {
 
 template <bool SEG>
 struct KeyGen {
-    const float *pts;
     const SegState *seg;
     const int *off;
     int nseg, shift;
     float lx, ly, lz, is, qmax;  // segment 0's grid (the single-segment case)
 
-    __device__ KeyGen(const float *p, const State *st, const SegState *sg, const int *o)
-        : pts(p), seg(sg), off(o), nseg(st->nseg), shift(3 * st->max_bits)
+    __device__ KeyGen(const State *st, const SegState *sg, const int *o)
+        : seg(sg), off(o), nseg(st->nseg), shift(3 * st->max_bits)
     {
         lx = sg[0].lo[0];
         ly = sg[0].lo[1];
@@ -31,15 +30,9 @@ struct KeyGen {
         qmax = (float)((1u << sg[0].bits) - 1u);
     }
 
-    // Key of input point i; `bad` is set if a coordinate is not finite.
-    __device__ __forceinline__ unsigned long long key(int64_t i, bool &bad) const
-    {
-        float4 p;
-        return key(i, bad, p);
-    }
-
-    // The same, also handing back the point as (x, y, z, i).
-    __device__ __forceinline__ unsigned long long key(int64_t i, bool &bad, float4 &pt) const
+    // Key of input point i at (x, y, z) (read by the caller); `bad` is set if
+    // a coordinate is not finite.
+    __device__ __forceinline__ unsigned long long key_of(int64_t i, float x, float y, float z, bool &bad) const
     {
         float x0 = lx, y0 = ly, z0 = lz, s = is, qm = qmax;
         unsigned long long top = 0;
@@ -53,8 +46,6 @@ struct KeyGen {
             qm = (float)((1u << g.bits) - 1u);
             top = (unsigned long long)sg << shift;
         }
-        const float x = __ldg(pts + 3 * i), y = __ldg(pts + 3 * i + 1), z = __ldg(pts + 3 * i + 2);
-        pt = make_float4(x, y, z, __int_as_float((int)i));
         bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
         const unsigned qx = quant_axis(x, x0, s, qm);
         const unsigned qy = quant_axis(y, y0, s, qm);
