@@ -56,7 +56,7 @@ def stage_bytes(stage: str, c: dict, n: int) -> float:
         "sort": (kb + kb + 4.0) + (P - 1) * 2 * (kb + 4.0),  # 1st pass: key in, key+idx out; then both ways
         "gather": 4.0 + 12.0 + 16.0,                      # perm, xyz, sorted float4 (the union-find
                                                           # resets are charged to the traversal's parent RMW)
-        "cells": 8.0 + 4.0,                               # keys, dense-root preset
+        "cells": (8.0 + 4.0) if c.get("dense_on", 1) else 0.0,  # keys, dense-root preset (no pass when off)
         "leaves": 4.0 + 4.0 + 16.0 + per_leaf * (32.0 + 16.0 + 1.0),  # dense root, leaf id, points; leaf records
         "build": per_leaf * (32.0 + 1.0 + 32.0 + 8.0 + 4.0 + 8.0),      # leaf box, delta, node, slot, child, rope
         "candidates": per_leaf * (32.0 + 16.0),                   # leaf record, candidate list (int4)

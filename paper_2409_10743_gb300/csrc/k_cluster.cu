@@ -66,8 +66,8 @@ static int g_cand_blocks_per_sm = 4;           // set per process by cluster_ini
 // Persistent: the walks differ in length by an order of magnitude, and a warp
 // runs as long as its longest walk, so each lane carries one walk at a time,
 // one node visit per step, and a lane whose walk ended takes the next leaf
-// from the warp's chunk of the leaf queue (chunks of 32 leaves: one global
-// atomic per 32 walks) -- the warp stays full until the queue runs dry.
+// from the warp's chunk of the leaf queue (chunks of CAND_CHUNK leaves: one
+// global atomic per chunk) -- the warp stays full until the queue runs dry.
 template <bool SEG>
 __global__ void __launch_bounds__(256, 6) k_cand(State *__restrict__ st, const SegState *__restrict__ seg,
                                               const int *__restrict__ leaf_seg, const float4 *__restrict__ nodes,
@@ -190,8 +190,14 @@ struct TravStats {
 // then, if the list overflowed, walks the ropes from the leaf where it ran out.
 // SCHED 2: no candidate lists; the point walks the ropes from its own leaf
 // with its own box, stopping early like k_cand (region_exit).
-template <int SCHED, bool FOF, bool STATS>
-__device__ __forceinline__ void union_query(const int i, const SegState &g, const Tree &T,
+// WARP: every lane of the warp calls this (points i of consecutive lanes are
+// consecutive), `active` says whether lane i queries, and the pairs inside
+// the own leaf (at most span + 1 consecutive points) are tested on the next
+// lanes' coordinates, fetched by shuffle with all lanes in step, instead of
+// by loads one after another.  Otherwise only querying threads call it.
+template <int SCHED, bool FOF, bool STATS, bool WARP>
+__device__ __forceinline__ void union_query(const int i, const bool active, const int span, const SegState &g,
+                                            const Tree &T,
                                             const float4 *__restrict__ spts, const int *__restrict__ leaf_of,
                                             const int4 *__restrict__ cand, int *parent, unsigned char *core,
                                             unsigned *dev_status, TravStats *stats)
@@ -226,7 +232,38 @@ __device__ __forceinline__ void union_query(const int i, const SegState &g, cons
         if (ld_cg(parent + j) != ri)
             ri = uf_unite(parent, spts, ri, j);
     };
-    if (own_end >= 0) {  // not a dense cell (its points are one set already)
+    if (WARP) {
+        const int lane = threadIdx.x & 31;
+        const int ci = FOF ? 1 : (int)core[i];
+        for (int d = 1; d <= span; d++) {
+            const float qx = __shfl_down_sync(~0u, p.x, d);
+            const float qy = __shfl_down_sync(~0u, p.y, d);
+            const float qz = __shfl_down_sync(~0u, p.z, d);
+            const int qc = FOF ? 1 : __shfl_down_sync(~0u, ci, d);
+            const int j = i + d;
+            if (active && j < own_end) {  // (never in a dense cell: DENSE_BIT makes own_end negative)
+                float4 q = make_float4(qx, qy, qz, 0.0f);
+                bool cj = qc != 0;
+                if (lane + d >= 32) {  // the leaf runs on past the warp
+                    q = __ldg(spts + j);
+                    cj = FOF || core[j];
+                }
+                if (STATS)
+                    c_test++;
+                if (cj && dist2_rn(p.x, p.y, p.z, q.x, q.y, q.z) <= e2) {
+                    link(j);
+                    if (STATS)
+                        c_union++;
+                    if (FOF) {
+                        found = true;
+                        core[j] = 1;
+                    }
+                }
+            }
+        }
+        if (!active)
+            return;
+    } else if (own_end >= 0) {  // not a dense cell (its points are one set already)
         const int e = own_end;
         for (int j = i + 1; j < e; j++) {
             float4 q = __ldg(spts + j);
@@ -358,16 +395,25 @@ __global__ void __launch_bounds__(1024, 2) k_union(int64_t n, const State *__res
                         const float4 *__restrict__ spts, const float4 *__restrict__ nodes,
                         const int *__restrict__ leaf_of, const int *__restrict__ leaf_first,
                         const int4 *__restrict__ cand, int *parent,
-                        unsigned char *core, unsigned *dev_status, TravStats *stats)
+                        unsigned char *core, unsigned *dev_status, TravStats *stats, int span)
 {
     const int64_t i64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i64 >= n)
-        return;
-    const int i = (int)i64;
-    if (!FOF && !core[i])
-        return;
     const Tree T{nodes, leaf_first, st->n_leaves};
-    union_query<SCHED, FOF, STATS>(i, seg[0], T, spts, leaf_of, cand, parent, core, dev_status, stats);
+    if (FOF) {  // (measured: the own-leaf loop beats the shuffles when few pairs are neighbours)
+        if (i64 < n)
+            union_query<SCHED, true, STATS, false>((int)i64, true, 0, seg[0], T, spts, leaf_of, cand, parent, core,
+                                                   dev_status, stats);
+        return;
+    }
+    if (i64 - (threadIdx.x & 31) >= n)
+        return;  // the whole warp is past the end
+    // DBSCAN: every lane takes part in the own-leaf shuffles; lanes past the
+    // end and non-core points only lend their coordinates
+    const bool in = i64 < n;
+    const int i = in ? (int)i64 : (int)n - 1;
+    const bool active = in && core[i];
+    union_query<SCHED, false, STATS, true>(i, active, span, seg[0], T, spts, leaf_of, cand, parent, core, dev_status,
+                                           stats);
 }
 
 // Many segments: each query takes its segment's eps and mode from its key.
@@ -386,9 +432,10 @@ __global__ void __launch_bounds__(1024, 2) k_union_seg(int64_t n, const State *_
     const SegState &g = seg[seg_of_key(sorted_key(st, k0, k1, i), st->shift)];
     const Tree T{nodes, leaf_first, st->n_leaves};
     if (g.minpts <= 2)
-        union_query<SCHED, true, STATS>(i, g, T, spts, leaf_of, cand, parent, core, dev_status, stats);
+        union_query<SCHED, true, STATS, false>(i, true, 0, g, T, spts, leaf_of, cand, parent, core, dev_status, stats);
     else if (core[i])
-        union_query<SCHED, false, STATS>(i, g, T, spts, leaf_of, cand, parent, core, dev_status, stats);
+        union_query<SCHED, false, STATS, false>(i, true, 0, g, T, spts, leaf_of, cand, parent, core, dev_status,
+                                                stats);
 }
 
 // ---- core counting with early termination (minPts > 2) -------------------------------
@@ -620,7 +667,7 @@ __global__ void __launch_bounds__(256) k_finalize(int64_t n, const State *__rest
 }
 
 template <int SCHED>
-static void launch_union(const Work &w, int g, int B, TravStats *stats, cudaStream_t s)
+static void launch_union(const Work &w, int g, int B, int span, TravStats *stats, cudaStream_t s)
 {
     if (w.nseg > 1) {
         if (stats)
@@ -635,20 +682,20 @@ static void launch_union(const Work &w, int g, int B, TravStats *stats, cudaStre
         if (stats)
             k_union<SCHED, true, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
                                                        w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
-                                                       w.dev_status, stats);
+                                                       w.dev_status, stats, span);
         else
             k_union<SCHED, true, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
                                                         w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
-                                                        w.dev_status, nullptr);
+                                                        w.dev_status, nullptr, span);
     } else {
         if (stats)
             k_union<SCHED, false, true><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
                                                         w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
-                                                        w.dev_status, stats);
+                                                        w.dev_status, stats, span);
         else
             k_union<SCHED, false, false><<<g, B, 0, s>>>(w.n, w.st, w.seg, w.keys[0], w.keys[1], w.spts, w.nodes,
                                                          w.leaf_of, w.leaf_first, w.cand, w.parent, w.core,
-                                                         w.dev_status, nullptr);
+                                                         w.dev_status, nullptr, span);
     }
     note_launch();
 }
@@ -681,9 +728,9 @@ void stage_cluster(const Work &w, const Params &p, int32_t *labels, cudaStream_t
         prof_mark(ST_COUNT, s);
     }
     if (p.schedule == 1)
-        launch_union<1>(w, g, B, stats, s);
+        launch_union<1>(w, g, B, p.leaf_size - 1, stats, s);
     else
-        launch_union<2>(w, g, B, stats, s);
+        launch_union<2>(w, g, B, p.leaf_size - 1, stats, s);
     prof_mark(ST_UNION, s);
     if (w.any_dbscan) {
         if (seg)
