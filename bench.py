@@ -49,7 +49,7 @@ def stage_bytes(stage: str, c: dict, n: int) -> float:
     per_leaf = L / n
     kb = 4.0 if c.get("key_bits", 64) == 32 else 8.0  # key bytes
     table = {
-        "bounds": 12.0,                                   # read xyz
+        "bounds": 12.0 if n < (1 << 22) else 12.0 / 32,   # read xyz (every 32nd point from 2^22 points on)
         "morton": 12.0 + kb,                              # read xyz, write key
         # inputs above 2^23 points: key + point in, key + (point, index) out, by the key's top bits
         "bucket": (kb + 12.0 + kb + 16.0) if n >= (1 << 23) else 0.0,

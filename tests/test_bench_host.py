@@ -28,9 +28,15 @@ def test_stage_bytes_table():
     assert bench.stage_bytes("union", c32, n) == pytest.approx(25 + 64 * per_leaf)
     assert bench.stage_bytes("candidates", c32, n) == pytest.approx(48 * per_leaf)
     assert bench.stage_bytes("no-such-stage", c32, n) == 0
-    names = ["bounds", "morton", "sort", "gather", "cells", "leaves", "build", "candidates", "union", "finalize"]
+    # bounds: every point below 2^22 points, every 32nd above
+    assert bench.stage_bytes("bounds", c32, n) == pytest.approx(12 / 32)
+    assert bench.stage_bytes("bounds", c32, 1 << 20) == 12
+    # no dense-cell pass when dense cells are off
+    assert bench.stage_bytes("cells", dict(c32, dense_on=0), n) == 0 and bench.stage_bytes("cells", c32, n) == 12
+    names = ["bounds", "morton", "bucket", "sort", "gather", "cells", "leaves", "build", "candidates", "union",
+             "finalize"]
     total = sum(bench.stage_bytes(k, c32, n) for k in names)
-    assert 250 < total < 330  # the FoF step on the 2^27-point workload: about 290 B per point
+    assert 250 < total < 330  # the FoF step on the 2^27-point workload: about 275 B per point
 
 
 def test_kernel_source_hash_follows_the_include_chain(tmp_path, monkeypatch):
