@@ -352,10 +352,10 @@ typedef struct abx_server abx_server;
 /* Create a server (cfg may be NULL for defaults).  Host-resident requests'
  * points are copied to the device straight from the caller's memory (or,
  * with ABX_SERVE_STAGING=1, staged through pinned buffers first); their
- * labels come back through pinned buffers, allocated once per slot, at its
- * first host request, for max_batch_points labels (with staging, points
- * too): max_slots x max_batch_points x 4 bytes of pinned host memory (x 16
- * with staging).  Host-side fault injection for
+ * labels come back through pinned buffers, allocated per slot at its first
+ * host request for min(max_batch_points, 2^25) labels (with staging, points
+ * too) and grown only by a larger batch: max_slots x 4 bytes per point of
+ * pinned host memory (16 with staging).  Host-side fault injection for
  * tests: ABX_SERVE_FAULT=hold admits nothing, =alloc fails every batch's
  * device allocation.  (Both read at creation.) */
 abx_status abx_serve_create(const abx_serve_config *cfg, abx_server **out);

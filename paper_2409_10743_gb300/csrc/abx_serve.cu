@@ -207,9 +207,10 @@ void launch_slot(abx_server *sv, Slot &sl)
         sl.h_pts = nullptr;
         sl.h_lab = nullptr;
         sl.cap = 0;
-        // once, at the batch size limit: pinning memory takes long enough to
-        // show in the latency of the batch that would wait for it
-        const int64_t cap = std::max<int64_t>(sl.total, sv->cfg.max_batch_points);
+        // once, at the batch size limit (up to 2^25 points; past that, as
+        // large as the batch): pinning memory takes long enough to show in
+        // the latency of the batch that would wait for it
+        const int64_t cap = std::max<int64_t>(sl.total, std::min<int64_t>(sv->cfg.max_batch_points, 1ll << 25));
         if ((sv->stage_points && cudaMallocHost((void **)&sl.h_pts, (size_t)cap * 3 * sizeof(float)) != cudaSuccess) ||
             cudaMallocHost((void **)&sl.h_lab, (size_t)cap * sizeof(int32_t)) != cudaSuccess) {
             cudaGetLastError();
