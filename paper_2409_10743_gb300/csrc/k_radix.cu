@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_morton(const float *__restrict__ pts, i
     const KeyGen<SEG> kg(st, seg, off);
     __syncthreads();
     auto one = [&](int64_t i, float x, float y, float z) {
-        const u64 key = kg.key_of(i, x, y, z, bad);
+        const u64 key = kg.template key_of<K>(i, x, y, z, bad);
         if (write_keys)
             keys[i] = (K)key;
         for (int p = 0; p < np; p++)

@@ -13,6 +13,17 @@
 
 namespace abx {
 
+// spread3 for values below 2^10, in 32-bit arithmetic: bit k goes to bit 3k.
+__device__ __forceinline__ unsigned spread3_10(unsigned v)
+{
+    unsigned x = v & 0x3ffu;
+    x = (x | x << 16) & 0x030000ffu;
+    x = (x | x << 8) & 0x0300f00fu;
+    x = (x | x << 4) & 0x030c30c3u;
+    x = (x | x << 2) & 0x09249249u;
+    return x;
+}
+
 template <bool SEG>
 struct KeyGen {
     const SegState *seg;
@@ -31,7 +42,9 @@ struct KeyGen {
     }
 
     // Key of input point i at (x, y, z) (read by the caller); `bad` is set if
-    // a coordinate is not finite.
+    // a coordinate is not finite.  K = 32-bit keys: at most 10 bits per axis,
+    // interleaved in 32-bit arithmetic (the same bits as spread3's).
+    template <typename K>
     __device__ __forceinline__ unsigned long long key_of(int64_t i, float x, float y, float z, bool &bad) const
     {
         float x0 = lx, y0 = ly, z0 = lz, s = is, qm = qmax;
@@ -50,6 +63,8 @@ struct KeyGen {
         const unsigned qx = quant_axis(x, x0, s, qm);
         const unsigned qy = quant_axis(y, y0, s, qm);
         const unsigned qz = quant_axis(z, z0, s, qm);
+        if (sizeof(K) == 4)
+            return top | ((spread3_10(qx) << 2) | (spread3_10(qy) << 1) | spread3_10(qz));
         return top | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     }
 };
