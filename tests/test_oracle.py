@@ -187,6 +187,44 @@ def test_exact_translation():
     assert np.array_equal(oracle.dbscan(p, eps, 3), oracle.dbscan(q, eps, 3))
 
 
+# ---- a closed form: the unit cubic lattice at eps = 1 ----------------------------------
+
+def _lattice_expected(n, minpts, order):
+    """Labels of the n^3 unit lattice at eps = 1, derived by hand: a point's
+    neighbours are itself and its axis neighbours inside the lattice (the
+    diagonal ones are sqrt(2) away), so |N| = 7 - (faces of the cube the
+    point lies on).  minPts 2: one cluster.  minPts 7: the interior points
+    are core and linked along the axes; a point on exactly one face touches
+    the interior point behind it (a border point); edge and corner points
+    touch only non-core points (noise).  Ids are the smallest member index
+    in the given order."""
+    g = np.stack(np.meshgrid(*[np.arange(n)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    on_faces = ((g == 0) | (g == n - 1)).sum(1)
+    if minpts == 2:
+        member = np.ones(len(g), bool)
+    else:
+        assert minpts == 7
+        member = on_faces <= 1
+    want = np.full(len(g), -1, np.int32)
+    pos = np.empty(len(g), np.int64)
+    pos[order] = np.arange(len(g))            # index of lattice point k in the shuffled input
+    want[member] = pos[member].min()
+    return g, want, pos
+
+
+@pytest.mark.parametrize("n,minpts", [(2, 2), (5, 2), (5, 7), (9, 7), (3, 7)])
+def test_unit_lattice_closed_form(n, minpts):
+    rng = np.random.default_rng(n * 10 + minpts)
+    order = rng.permutation(n ** 3)
+    g, want, pos = _lattice_expected(n, minpts, order)
+    p = g[order].astype(np.float32)
+    got = oracle.dbscan(p, 1.0, minpts)
+    assert np.array_equal(got[pos], want)
+    # just below 1 nothing is a neighbour: every point alone, hence noise
+    below = float(np.nextafter(np.float32(1.0), np.float32(0.0)))
+    assert (oracle.dbscan(p, below, 2) == -1).all()
+
+
 # ---- argument checking ---------------------------------------------------------------
 
 def test_errors():
