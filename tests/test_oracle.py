@@ -273,8 +273,8 @@ def _pins_pass(lib_dbscan) -> bool:
     return True
 
 
-@pytest.mark.parametrize("mut", MUTATIONS, ids=lambda m: m[0])
-def test_planted_mistake_is_caught(mut, tmp_path):
+def _mutated(mut, tmp_path):
+    """The oracle with one planted mistake, as a labels(p, eps, minpts) call."""
     import ctypes
     name, old, new = mut
     src = open(os.path.join(os.path.dirname(oracle.__file__), "dbscan_oracle.c")).read()
@@ -294,4 +294,27 @@ def test_planted_mistake_is_caught(mut, tmp_path):
         rc = lib.oracle_dbscan(p.ctypes.data, len(p), float(np.float32(eps)), minpts, lab.ctypes.data)
         return lab if rc == 0 else None
 
-    assert not _pins_pass(run), f"planted mistake not caught: {name}"
+    return run
+
+
+@pytest.mark.parametrize("mut", MUTATIONS, ids=lambda m: m[0])
+def test_planted_mistake_is_caught(mut, tmp_path):
+    assert not _pins_pass(_mutated(mut, tmp_path)), f"planted mistake not caught: {mut[0]}"
+
+
+# mistakes the lattice's closed form catches on its own (the other three do
+# not change its labels: one cluster, and no core point next to a noise point)
+LATTICE_CATCHES = ["open neighbourhood", "dropped z term", "wrong sign in dy", "row offset off by one",
+                   "cell too small", "core strict", "border id ignored"]
+
+
+@pytest.mark.parametrize("mut", [m for m in MUTATIONS if m[0] in LATTICE_CATCHES], ids=lambda m: m[0])
+def test_lattice_closed_form_alone_catches(mut, tmp_path):
+    run = _mutated(mut, tmp_path)
+    for n, minpts in [(2, 2), (5, 2), (5, 7), (9, 7), (3, 7)]:
+        order = np.random.default_rng(n * 10 + minpts).permutation(n ** 3)
+        g, want, pos = _lattice_expected(n, minpts, order)
+        got = run(g[order].astype(np.float32), 1.0, minpts)
+        if got is None or not np.array_equal(got[pos], want):
+            return
+    raise AssertionError(f"the lattice's closed form missed: {mut[0]}")
