@@ -225,6 +225,16 @@ def test_unit_lattice_closed_form(n, minpts):
     assert (oracle.dbscan(p, below, 2) == -1).all()
 
 
+@pytest.mark.parametrize("n,minpts", [(1, 1), (1, 2), (40, 40), (40, 41), (500, 7)])
+def test_eps_beyond_the_diagonal(n, minpts):
+    """eps = 2 exceeds the unit cube's diagonal: every pair is a neighbour pair,
+    |N| = n for every point, so all points form one cluster with id 0 when
+    n >= minPts and are all noise otherwise."""
+    p = np.random.default_rng(n + minpts).random((n, 3), dtype=np.float32)
+    want = np.zeros(n, np.int32) if n >= minpts else np.full(n, -1, np.int32)
+    assert np.array_equal(oracle.dbscan(p, 2.0, minpts), want)
+
+
 # ---- argument checking ---------------------------------------------------------------
 
 def test_errors():
